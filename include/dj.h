@@ -1,0 +1,266 @@
+/*
+ * dj.h -- C ABI of the GB300 dense adjacency-matrix Dijkstra library.
+ *
+ * The operation is the paper's Algorithm 1 (Section III-A, "Serial Dijkstra's
+ * Algorithm"): from a source s, n outer steps each take the unvisited node u
+ * of smallest dist, mark it visited, and relax row u of the n x n weight
+ * matrix G with  dist[v] = dist[u] + G[u][v], pred[v] = u  whenever that is a
+ * strict improvement.  Inputs are edge lists turned into the matrix as in
+ * Section III (Empirical methodology) and the -w flag of Section III-A.
+ *
+ * Results are defined as Algorithm 1's, read as follows where the paper is
+ * silent: ties in the argmin go to the smallest index; pred starts at -1 (the
+ * source and unreachable nodes keep -1); infinity is DJ_INF (INT32_MAX), also
+ * the dist of unreachable nodes.  All arithmetic is int32; results are exact.
+ *
+ * Conventions for every call:
+ *   - Return value: DJ_OK (0) or a negative DJ_E* status.  dj_last_error()
+ *     returns a thread-local message for the last failing call on this thread.
+ *   - `stream` is a cudaStream_t cast to uint64_t (0 = the legacy default
+ *     stream).  Calls marked "asynchronous" only enqueue work on that stream;
+ *     device-side failures (a bounded in-kernel wait that ran out) are
+ *     reported by the next dj_sync() on the device.
+ *   - "device pointer" means memory of the current CUDA device (for instance a
+ *     torch tensor's data_ptr()); "host pointer" means ordinary host memory.
+ *     Buffers stay owned by the caller unless stated otherwise.
+ *   - The library keeps no global state other than a per-device context
+ *     (error word, SM count) created on first use.
+ */
+#ifndef DJ_H
+#define DJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define DJ_OK 0
+#define DJ_EINVAL (-1)       /* bad argument: id out of range, negative or DJ_INF weight, n < 1 ... */
+#define DJ_ENOMEM (-2)       /* device or pinned allocation failed, or over the serving HBM budget */
+#define DJ_EOVERFLOW (-3)    /* (n-1) * max weight >= INT32_MAX: a path length could overflow int32 */
+#define DJ_ECUDA (-4)        /* a CUDA runtime call failed (message in dj_last_error) */
+#define DJ_ETIMEOUT (-5)     /* a bounded in-kernel wait ran out; the kernel returned early */
+#define DJ_EBUSY (-6)        /* serving: no free slot or budget for the request right now */
+#define DJ_EUNSUPPORTED (-7) /* configuration the device cannot run (e.g. cluster size) */
+
+#define DJ_INF 2147483647
+
+const char* dj_last_error(void);
+const char* dj_status_string(int status);
+int dj_version(void); /* major*10000 + minor*100 + patch */
+
+/* ------------------------------------------------------------------ graphs */
+typedef struct dj_graph dj_graph;
+
+typedef struct dj_graph_info {
+  int32_t n;             /* nodes */
+  int32_t pitch;         /* row stride of the device matrix in int32 elements (n rounded up to 32) */
+  int32_t directed;      /* 1 if built with the -w (directed) fill */
+  int32_t min_weight;    /* smallest finite off-diagonal weight, DJ_INF if the graph has no edge */
+  int32_t max_weight;    /* largest finite off-diagonal weight, 0 if none */
+  int32_t device;        /* CUDA device holding the matrix */
+  const int32_t* matrix; /* device pointer: n rows x pitch int32, row-major; columns >= n hold DJ_INF */
+  const int32_t* minout; /* device pointer: n int32, min finite off-diagonal weight of row u (DJ_INF if none) */
+  uint64_t bytes;        /* device bytes owned by the graph */
+} dj_graph_info;
+
+/* Build the n x n matrix on the current device from an edge list (Section
+ * III: edge lists are written into the adjacency matrix; Section III-A
+ * footnote: -w fills a directed graph, otherwise undirected).
+ *   n          nodes, >= 1
+ *   m          edges, >= 0
+ *   src,dst,w  HOST pointers to m int32 each; read during the call only.
+ *              Ids are 0-based in [0, n); 0 <= w < DJ_INF.
+ *   directed   0: G[u][v] = G[v][u] = w;  1 (the paper's -w): G[u][v] = w only
+ * The diagonal is 0, missing entries DJ_INF, a repeated pair keeps its minimum
+ * weight, self-loops are ignored.  On success *out owns the device matrix until
+ * dj_graph_free.  Synchronous with respect to the host (the edge arrays may be
+ * reused on return); the device work is ordered on `stream`.
+ * Errors: DJ_EINVAL (bad id/weight/n/m, NULL pointer), DJ_EOVERFLOW
+ * ((n-1) * max weight >= INT32_MAX), DJ_ENOMEM, DJ_ECUDA. */
+int dj_load_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                  int directed, uint64_t stream, dj_graph** out);
+
+/* Build a graph from an n x n row-major matrix W with row stride ld >= n
+ * (same entry rules as above: diagonal must be 0, entries in [0, DJ_INF]).
+ * `w_on_device` says whether W is a device (1) or host (0) pointer.  The
+ * matrix is copied; the caller keeps W.  Errors as dj_load_edges (the entry
+ * check runs on the device and reports DJ_EINVAL). Synchronous. */
+int dj_load_dense(int32_t n, const int32_t* W, int64_t ld, int w_on_device, uint64_t stream,
+                  dj_graph** out);
+
+/* Overwrite an existing graph's matrix with a new n x n matrix of the same n
+ * (host pointer W, row stride ld), then recompute its row minima.  This is the
+ * host-to-device matrix copy of the paper's CUDA accounting (Section III-C,
+ * "Memory allocation and data transfer") without a new allocation.  The copy
+ * is asynchronous on `stream` when W is pinned; entries are not re-validated
+ * (callers pass matrices that came from dj_graph_download or a validated load). */
+int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64_t stream);
+
+/* Copy the n x n matrix to HOST memory W (row stride ld >= n); synchronous. */
+int dj_graph_download(const dj_graph* g, int32_t* W, int64_t ld, uint64_t stream);
+
+int dj_graph_get_info(const dj_graph* g, dj_graph_info* info);
+
+/* Release the device matrix.  The caller must have synchronised every stream
+ * that still uses g.  NULL is accepted. */
+int dj_graph_free(dj_graph* g);
+
+/* ------------------------------------------------------------------ single solve */
+#define DJ_MODE_AUTO 0  /* = DJ_MODE_PHASE */
+#define DJ_MODE_PHASE 1 /* exact phase-batched: settles every node provably next in Algorithm 1's
+                           visit order in one fused relaxation pass (same dist and pred) */
+#define DJ_MODE_PLAIN 2 /* literal Algorithm 1: one argmin + one row relaxation per step */
+
+#define DJ_ENGINE_AUTO 0
+#define DJ_ENGINE_GRID 1    /* one cooperative persistent kernel over every SM; column slices per CTA */
+#define DJ_ENGINE_CLUSTER 2 /* one thread-block cluster; state in distributed shared memory */
+
+typedef struct dj_solve_opts {
+  int32_t mode;           /* DJ_MODE_* */
+  int32_t engine;         /* DJ_ENGINE_* */
+  int32_t cluster_size;   /* cluster engine: CTAs per cluster (1..16), 0 = auto */
+  int32_t threads;        /* threads per CTA (256, 512 or 1024), 0 = auto */
+  int32_t ctas_per_sm;    /* grid engine: resident CTAs per SM (1 or 2), 0 = auto */
+  int32_t unroll;         /* rows in flight per warp (1, 2, 4 or 8), 0 = auto */
+  int64_t timeout_ns;     /* limit of every in-kernel wait, 0 = 2 s */
+  int32_t debug_skip_cta; /* testing only: this CTA leaves before the first grid barrier (-1 = none) */
+  int32_t reserved[5];
+} dj_solve_opts;
+
+/* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */
+void dj_solve_opts_init(dj_solve_opts* opts);
+
+/* One solve of Algorithm 1 from `source` on graph g.
+ *   dist, pred  DEVICE pointers to n int32 each (caller-owned), written by the kernel.
+ * Asynchronous on `stream`.  Errors: DJ_EINVAL (source out of range, NULL),
+ * DJ_ECUDA (launch failed); a device-side timeout shows at dj_sync(). */
+int dj_sssp(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
+int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
+               const dj_solve_opts* opts, uint64_t stream);
+
+/* The same solve with HOST result buffers (n int32 each): launches, copies
+ * dist and pred back, synchronises `stream` and returns the device status
+ * (DJ_ETIMEOUT included).  Pinned buffers give the fastest copy. */
+int dj_sssp_host(const dj_graph* g, int32_t source, int32_t* dist_host, int32_t* pred_host,
+                 uint64_t stream);
+
+/* Synchronise `stream`, then return and clear the device error word of the
+ * current device: DJ_ETIMEOUT if a bounded wait ran out since the last
+ * dj_sync, DJ_ECUDA on a CUDA error, DJ_OK otherwise. */
+int dj_sync(uint64_t stream);
+
+/* Phases (fused relaxation passes) taken by the last completed solve launched
+ * by dj_sssp/dj_sssp_ex on this device; -1 if unknown.  Call after dj_sync. */
+int dj_last_phases(void);
+
+/* ------------------------------------------------------------------ batched solves */
+/* k solves (graph[i], sources[i]) in ONE persistent launch: one thread-block
+ * cluster per solve at a time, solves pulled from a device queue (largest n
+ * first), graphs of different n allowed.  Rows shared by concurrent solves of
+ * one graph are reused through L2.  Each solve's result equals dj_sssp's.
+ *   graphs   HOST array of k graph handles (all on the current device)
+ *   sources  HOST array of k int32
+ *   dist, pred  HOST arrays of k DEVICE pointers, n_i int32 each
+ * Asynchronous on `stream` (the descriptor table is copied before return). */
+int dj_sssp_batch(const dj_graph* const* graphs, const int32_t* sources, int32_t k,
+                  int32_t* const* dist, int32_t* const* pred, uint64_t stream);
+
+typedef struct dj_batch_opts {
+  int32_t mode;          /* DJ_MODE_* */
+  int32_t cluster_size;  /* 0 = auto (autotuned table or heuristic) */
+  int32_t threads;       /* 0 = auto */
+  int32_t clusters;      /* clusters resident at once, 0 = as many as fit */
+  int32_t reserved[8];
+} dj_batch_opts;
+
+void dj_batch_opts_init(dj_batch_opts* opts);
+
+/* A prepared batch: the descriptor table lives on the device, so launching it
+ * is a single kernel launch plus a 64-byte memset, both capturable in a CUDA
+ * graph.  The caller keeps the graphs and result buffers alive while launched. */
+typedef struct dj_batch dj_batch;
+int dj_batch_create(const dj_graph* const* graphs, const int32_t* sources, int32_t k,
+                    int32_t* const* dist, int32_t* const* pred, const dj_batch_opts* opts,
+                    dj_batch** out);
+int dj_batch_launch(dj_batch* b, uint64_t stream);
+int dj_batch_free(dj_batch* b); /* caller synchronises first */
+
+/* Autotuner: times every supported (cluster size, threads) pair for this
+ * batch on the device and stores the fastest in the batch (and in the
+ * process-wide table keyed by (n bucket, density bucket, SM count), which
+ * DJ_MODE_AUTO batches consult).  Synchronous; overwrites the batch's outputs.
+ * Reports the choice through the optional out-parameters. */
+int dj_batch_autotune(dj_batch* b, uint64_t stream, int32_t* cluster_size, int32_t* threads,
+                      float* best_ms);
+
+/* ------------------------------------------------------------------ serving */
+typedef struct dj_server dj_server;
+
+typedef struct dj_serve_opts {
+  uint64_t hbm_budget;   /* bytes of device memory the server may hold (graphs + result pool) */
+  int32_t max_slots;     /* requests in flight on the device at most (<= 4096) */
+  int32_t cluster_size;  /* CTAs per solve cluster, 0 = auto */
+  int32_t threads;       /* 0 = auto */
+  int32_t clusters;      /* persistent solve clusters, 0 = as many as fit */
+  int64_t idle_timeout_ns; /* the persistent kernel exits after this long without work, 0 = 200 ms */
+  int32_t reserved[8];
+} dj_serve_opts;
+
+typedef struct dj_serve_stats {
+  uint64_t submitted, completed, rejected;
+  double p50_us, p90_us, p99_us, max_us, mean_us; /* submit-to-completion latency */
+  double solves_per_s;                            /* completed / (last completion - first submit) */
+  uint64_t resident_bytes;                        /* graphs + result pool held on the device */
+  int32_t kernel_launches;                        /* persistent kernel (re)launches so far */
+  int32_t reserved[7];
+} dj_serve_stats;
+
+void dj_serve_opts_init(dj_serve_opts* opts);
+
+/* Create a server on the current device.  Allocates the pinned request ring
+ * and completion words; device memory is admitted against hbm_budget. */
+int dj_serve_create(const dj_serve_opts* opts, dj_server** out);
+
+/* Make graph g resident for serving (counted against the budget); *graph_id
+ * names it in requests.  DJ_ENOMEM if it does not fit the budget. */
+int dj_serve_add_graph(dj_server* s, const dj_graph* g, int32_t* graph_id);
+
+/* Submit one solve.  dist/pred are DEVICE or mapped-pinned HOST pointers of
+ * n int32 each, or both NULL (the result then lands in a server-owned pool
+ * buffer, counted against the budget, readable with dj_serve_result until the
+ * next submit reuses it).  Returns DJ_EBUSY when every slot or the budget is
+ * taken (the caller retries after a poll); the request then was not queued. */
+int dj_serve_submit(dj_server* s, int32_t graph_id, int32_t source, int32_t* dist, int32_t* pred,
+                    uint64_t* ticket);
+
+/* *done = 1 once the ticket's result is in place (0 otherwise). */
+int dj_serve_poll(dj_server* s, uint64_t ticket, int* done);
+
+/* Block until the ticket completes or timeout_ns passes (DJ_ETIMEOUT). */
+int dj_serve_wait(dj_server* s, uint64_t ticket, int64_t timeout_ns);
+
+/* Copy a completed pool-buffered result to HOST memory (n int32 each). */
+int dj_serve_result(dj_server* s, uint64_t ticket, int32_t* dist_host, int32_t* pred_host);
+
+int dj_serve_stats_get(dj_server* s, dj_serve_stats* st);
+int dj_serve_destroy(dj_server* s); /* waits for in-flight work */
+
+/* Run a whole request trace on a fresh server: request r (graph req_graph[r],
+ * source req_source[r]) is submitted no earlier than arrival_s[r] seconds
+ * after the start (HOST arrays of R entries), admitted as slots and budget
+ * free up, and completed by the persistent kernel while later requests keep
+ * arriving (continuous batching).  out_dist/out_pred are optional HOST arrays
+ * of R device pointers (entries may be NULL to drop that result).  Fills *st. */
+int dj_serve(const dj_graph* const* graphs, int32_t num_graphs, int64_t R, const int32_t* req_graph,
+             const int32_t* req_source, const double* arrival_s, int32_t* const* out_dist,
+             int32_t* const* out_pred, const dj_serve_opts* opts, dj_serve_stats* st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DJ_H */

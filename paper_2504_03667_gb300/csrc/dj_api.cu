@@ -1,0 +1,427 @@
+// C ABI glue: error reporting, the per-device context, single solves and
+// batched solves.  Every entry point validates its arguments on the host and
+// only then enqueues device work.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "dj_common.cuh"
+#include "dj_internal.h"
+
+namespace dj {
+
+static thread_local std::string g_last_error;
+
+int set_error(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+int cuda_error(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return DJ_ECUDA;
+}
+void clear_error() { g_last_error.clear(); }
+
+static std::mutex g_ctx_mu;
+static DevCtx g_ctx[64];
+
+int get_ctx(DevCtx** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice (is a CUDA GPU present?)");
+  if (dev < 0 || dev >= 64) return set_error(DJ_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  DevCtx& c = g_ctx[dev];
+  if (c.device != dev) {
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+    if (prop.major < 10) return set_error(DJ_EUNSUPPORTED, "this library targets sm_103a (Blackwell) devices");
+    c.num_sms = prop.multiProcessorCount;
+    c.max_smem_optin = static_cast<int>(prop.sharedMemPerBlockOptin);
+    c.coop = prop.cooperativeLaunch;
+    int cl = 0;
+    cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, dev);
+    c.cluster_launch = cl;
+    e = cudaMalloc(&c.words, 64 * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(device words)");
+    e = cudaMemset(c.words, 0, 64 * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemset(device words)");
+    c.device = dev;
+  }
+  *out = &c;
+  return DJ_OK;
+}
+
+}  // namespace dj
+
+using namespace dj;
+
+extern "C" const char* dj_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* dj_status_string(int status) {
+  switch (status) {
+    case DJ_OK: return "ok";
+    case DJ_EINVAL: return "invalid argument";
+    case DJ_ENOMEM: return "out of memory";
+    case DJ_EOVERFLOW: return "path lengths could overflow int32";
+    case DJ_ECUDA: return "CUDA error";
+    case DJ_ETIMEOUT: return "in-kernel wait timed out";
+    case DJ_EBUSY: return "busy";
+    case DJ_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+extern "C" int dj_version(void) { return 10000; }
+
+extern "C" void dj_solve_opts_init(dj_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->debug_skip_cta = -1;
+}
+
+extern "C" void dj_batch_opts_init(dj_batch_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+}
+
+// ------------------------------------------------------------------ single solves
+
+// Size below which one cluster beats the whole-GPU grid engine (fewer, cheaper barriers).
+static constexpr int32_t kGridMinN = 4096;
+
+static int default_cluster_size(int32_t n) {
+  (void)n;
+  return 8;
+}
+
+static int solve_cluster_single(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
+                                const dj_solve_opts& o, cudaStream_t st) {
+  ClusterLaunch cl;
+  cl.cluster_size = o.cluster_size > 0 ? o.cluster_size : default_cluster_size(g->n);
+  cl.clusters = 1;
+  const SolveDesc d = make_desc(g, source, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0);
+  uint8_t* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, 128, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(cluster workspace)");
+  e = cudaMemcpyAsync(ws, &d, sizeof(d), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "descriptor copy");
+  int rc = launch_cluster(reinterpret_cast<SolveDesc*>(ws), 1, g->n, g->pitch, reinterpret_cast<uint32_t*>(ws + 64),
+                          cl, st);
+  cudaFreeAsync(ws, st);
+  if (rc == DJ_OK) {
+    // keep the "phases" word meaningful only for the grid engine
+    DevCtx* ctx = nullptr;
+    if (get_ctx(&ctx) == DJ_OK) cudaMemsetAsync(ctx->words + 1, 0xFF, sizeof(uint32_t), st);
+  }
+  return rc;
+}
+
+extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts* opts,
+                          uint64_t stream) {
+  clear_error();
+  if (!g || !dist || !pred) return set_error(DJ_EINVAL, "NULL argument");
+  if (source < 0 || source >= g->n) return set_error(DJ_EINVAL, "source outside [0, n)");
+  dj_solve_opts o;
+  dj_solve_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.mode < DJ_MODE_AUTO || o.mode > DJ_MODE_PLAIN) return set_error(DJ_EINVAL, "unknown mode");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int engine = o.engine;
+  if (engine == DJ_ENGINE_AUTO) engine = g->n >= kGridMinN ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;
+  if (engine == DJ_ENGINE_GRID) return launch_grid(g, source, dist, pred, o, st);
+  if (engine == DJ_ENGINE_CLUSTER) return solve_cluster_single(g, source, dist, pred, o, st);
+  return set_error(DJ_EINVAL, "unknown engine");
+}
+
+extern "C" int dj_sssp(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream) {
+  return dj_sssp_ex(g, source, dist, pred, nullptr, stream);
+}
+
+extern "C" int dj_sync(uint64_t stream) {
+  clear_error();
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  uint32_t bits = 0;
+  e = cudaMemcpy(&bits, ctx->words, sizeof(bits), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "reading the device error word");
+  if (bits) {
+    cudaMemset(ctx->words, 0, sizeof(uint32_t));
+    if (bits & kErrTimeout) return set_error(DJ_ETIMEOUT, "a bounded in-kernel wait ran out; the kernel returned early");
+    return set_error(DJ_ECUDA, "device reported error bits " + std::to_string(bits));
+  }
+  return DJ_OK;
+}
+
+extern "C" int dj_last_phases(void) {
+  DevCtx* ctx = nullptr;
+  if (get_ctx(&ctx)) return -1;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, ctx->words + 1, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return v == 0xFFFFFFFFu ? -1 : static_cast<int>(v);
+}
+
+extern "C" int dj_sssp_host(const dj_graph* g, int32_t source, int32_t* dist_host, int32_t* pred_host,
+                            uint64_t stream) {
+  clear_error();
+  if (!g || !dist_host || !pred_host) return set_error(DJ_EINVAL, "NULL argument");
+  if (source < 0 || source >= g->n) return set_error(DJ_EINVAL, "source outside [0, n)");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int32_t* buf = nullptr;
+  const size_t bytes = static_cast<size_t>(g->n) * sizeof(int32_t);
+  cudaError_t e = cudaMallocAsync(&buf, 2 * bytes, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(results)");
+  int rc = dj_sssp(g, source, buf, buf + g->n, stream);
+  if (rc == DJ_OK) {
+    cudaMemcpyAsync(dist_host, buf, bytes, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(pred_host, buf + g->n, bytes, cudaMemcpyDeviceToHost, st);
+  }
+  cudaFreeAsync(buf, st);
+  if (rc != DJ_OK) return rc;
+  return dj_sync(stream);
+}
+
+// ------------------------------------------------------------------ batches
+
+struct dj_batch {
+  int device = 0;
+  int32_t k = 0;
+  int32_t max_n = 0;
+  int32_t max_pitch = 0;
+  SolveDesc* descs = nullptr;  // device, sorted by decreasing n
+  uint32_t* queue = nullptr;   // device word
+  ClusterLaunch cl;
+  ClusterPlan plan;
+  bool tuned = false;
+};
+
+// Autotuned choices per (n bucket, density bucket, SM count), process-wide.
+struct TuneKey {
+  int nb, db, sms;
+  bool operator==(const TuneKey& o) const { return nb == o.nb && db == o.db && sms == o.sms; }
+};
+struct TuneVal {
+  int cluster_size, threads;
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+
+static int n_bucket(int32_t n) {
+  int b = 0;
+  while ((1 << (b + 1)) <= n && b < 30) ++b;
+  return b;
+}
+
+static int heuristic_cluster_size(int32_t max_pitch) {
+  // wide enough slices for long row segments, small enough to keep many solves in flight
+  if (max_pitch >= 8192) return 8;
+  if (max_pitch >= 2048) return 4;
+  return 2;
+}
+
+static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, int32_t k, int32_t* const* dist,
+                       int32_t* const* pred, int plain, int device, std::vector<SolveDesc>* h, int32_t* max_n,
+                       int32_t* max_pitch);
+
+extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sources, int32_t k,
+                               int32_t* const* dist, int32_t* const* pred, const dj_batch_opts* opts, dj_batch** out) {
+  clear_error();
+  if (!out) return set_error(DJ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (k < 0 || (k > 0 && (!graphs || !sources || !dist || !pred))) return set_error(DJ_EINVAL, "NULL argument");
+  dj_batch_opts o;
+  dj_batch_opts_init(&o);
+  if (opts) o = *opts;
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  std::vector<SolveDesc> h;
+  int32_t max_n, max_pitch;
+  if (int rc = batch_descs(graphs, sources, k, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0, ctx->device, &h, &max_n,
+                           &max_pitch))
+    return rc;
+  auto* b = new dj_batch();
+  b->device = ctx->device;
+  b->k = k;
+  b->max_n = max_n;
+  b->max_pitch = max_pitch;
+  const size_t bytes = static_cast<size_t>(std::max(k, 1)) * sizeof(SolveDesc) + 64;
+  cudaError_t e = cudaMalloc(&b->descs, bytes);
+  if (e != cudaSuccess) {
+    delete b;
+    return set_error(DJ_ENOMEM, "cudaMalloc(batch descriptors)");
+  }
+  b->queue = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(b->descs) + static_cast<size_t>(std::max(k, 1)) * sizeof(SolveDesc));
+  if (k > 0) {
+    e = cudaMemcpy(b->descs, h.data(), static_cast<size_t>(k) * sizeof(SolveDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(b->descs);
+      delete b;
+      return cuda_error(e, "descriptor upload");
+    }
+  }
+  b->cl.cluster_size = o.cluster_size > 0 ? o.cluster_size : 0;
+  b->cl.threads = 256;
+  b->cl.clusters = o.clusters;
+  if (b->cl.cluster_size == 0) {
+    TuneKey key{n_bucket(max_n), 0, ctx->num_sms};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : g_tune)
+      if (kv.first == key) b->cl.cluster_size = kv.second.cluster_size;
+  }
+  if (b->cl.cluster_size == 0) b->cl.cluster_size = heuristic_cluster_size(max_pitch);
+  if (int rc = plan_cluster(b->max_pitch, b->cl, b->k, &b->plan)) {
+    cudaFree(b->descs);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return DJ_OK;
+}
+
+extern "C" int dj_batch_launch(dj_batch* b, uint64_t stream) {
+  clear_error();
+  if (!b) return set_error(DJ_EINVAL, "NULL batch");
+  if (b->k == 0) return DJ_OK;
+  return run_cluster(b->plan, b->descs, b->k, b->queue, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int dj_batch_free(dj_batch* b) {
+  clear_error();
+  if (!b) return DJ_OK;
+  cudaFree(b->descs);
+  delete b;
+  return DJ_OK;
+}
+
+extern "C" int dj_batch_autotune(dj_batch* b, uint64_t stream, int32_t* cluster_size, int32_t* threads,
+                                 float* best_ms) {
+  clear_error();
+  if (!b) return set_error(DJ_EINVAL, "NULL batch");
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  ClusterLaunch best_cl = b->cl;
+  const ClusterLaunch saved = b->cl;
+  for (int c : {2, 4, 8, 16}) {
+    ClusterLaunch cl = saved;
+    cl.cluster_size = c;
+    if (!cluster_config_ok(b->max_pitch, cl)) continue;
+    b->cl = cl;
+    if (plan_cluster(b->max_pitch, b->cl, b->k, &b->plan) != DJ_OK) {
+      clear_error();
+      continue;
+    }
+    float ms_sum = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      cudaEventRecord(e0, st);
+      if (dj_batch_launch(b, stream) != DJ_OK) ok = false;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;  // first run warms up
+    }
+    if (!ok) {
+      clear_error();
+      cudaGetLastError();
+      continue;
+    }
+    const float ms = ms_sum / 2.f;
+    if (ms < best) {
+      best = ms;
+      best_cl = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->cl = best_cl;
+  if (int rc = plan_cluster(b->max_pitch, b->cl, b->k, &b->plan)) return rc;
+  b->tuned = true;
+  {
+    TuneKey key{n_bucket(b->max_n), 0, ctx->num_sms};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool found = false;
+    for (auto& kv : g_tune)
+      if (kv.first == key) {
+        kv.second = TuneVal{best_cl.cluster_size, best_cl.threads};
+        found = true;
+      }
+    if (!found) g_tune.push_back({key, TuneVal{best_cl.cluster_size, best_cl.threads}});
+  }
+  if (cluster_size) *cluster_size = best_cl.cluster_size;
+  if (threads) *threads = best_cl.threads;
+  if (best_ms) *best_ms = best;
+  if (best >= 1e29f) return set_error(DJ_EUNSUPPORTED, "no cluster configuration could run");
+  return DJ_OK;
+}
+
+// Build the sorted descriptor table of a batch on the host.
+static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, int32_t k, int32_t* const* dist,
+                       int32_t* const* pred, int plain, int device, std::vector<SolveDesc>* h, int32_t* max_n,
+                       int32_t* max_pitch) {
+  h->resize(static_cast<size_t>(k));
+  *max_n = 1;
+  *max_pitch = 32;
+  for (int32_t i = 0; i < k; ++i) {
+    const dj_graph* g = graphs[i];
+    if (!g || !dist[i] || !pred[i]) return set_error(DJ_EINVAL, "NULL graph or result pointer at " + std::to_string(i));
+    if (g->device != device) return set_error(DJ_EINVAL, "graph on another device");
+    if (sources[i] < 0 || sources[i] >= g->n) return set_error(DJ_EINVAL, "source outside [0, n) at " + std::to_string(i));
+    (*h)[i] = make_desc(g, sources[i], dist[i], pred[i], plain);
+    *max_n = std::max(*max_n, g->n);
+    *max_pitch = std::max(*max_pitch, g->pitch);
+  }
+  std::stable_sort(h->begin(), h->end(), [](const SolveDesc& a, const SolveDesc& b) { return a.n > b.n; });
+  return DJ_OK;
+}
+
+extern "C" int dj_sssp_batch(const dj_graph* const* graphs, const int32_t* sources, int32_t k, int32_t* const* dist,
+                             int32_t* const* pred, uint64_t stream) {
+  clear_error();
+  if (k < 0 || (k > 0 && (!graphs || !sources || !dist || !pred))) return set_error(DJ_EINVAL, "NULL argument");
+  if (k == 0) return DJ_OK;
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  std::vector<SolveDesc> h;
+  int32_t max_n, max_pitch;
+  if (int rc = batch_descs(graphs, sources, k, dist, pred, 0, ctx->device, &h, &max_n, &max_pitch)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // stream-ordered table: allocated, filled, used and freed in stream order
+  uint8_t* ws = nullptr;
+  const size_t tbytes = static_cast<size_t>(k) * sizeof(SolveDesc);
+  cudaError_t e = cudaMallocAsync(&ws, tbytes + 64, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(batch descriptors)");
+  e = cudaMemcpyAsync(ws, h.data(), tbytes, cudaMemcpyHostToDevice, st);  // pageable: staged before return
+  if (e != cudaSuccess) {
+    cudaFreeAsync(ws, st);
+    return cuda_error(e, "descriptor upload");
+  }
+  ClusterLaunch cl;
+  cl.cluster_size = heuristic_cluster_size(max_pitch);
+  {
+    TuneKey key{n_bucket(max_n), 0, ctx->num_sms};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : g_tune)
+      if (kv.first == key) cl.cluster_size = kv.second.cluster_size;
+  }
+  int rc = launch_cluster(reinterpret_cast<SolveDesc*>(ws), k, max_n, max_pitch,
+                          reinterpret_cast<uint32_t*>(ws + tbytes), cl, st);
+  cudaFreeAsync(ws, st);
+  return rc;
+}

@@ -1,0 +1,95 @@
+// Host-side internals shared by the translation units of libdj.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/dj.h"
+
+struct dj_graph {
+  int32_t n = 0;
+  int32_t pitch = 0;  // row stride in int32 (n rounded up to 32)
+  int32_t directed = 0;
+  int32_t device = 0;
+  int32_t wmin = DJ_INF;  // smallest finite off-diagonal weight
+  int32_t wmax = 0;       // largest finite off-diagonal weight
+  int32_t* W = nullptr;       // n x pitch, row-major
+  int32_t* minout = nullptr;  // n
+  uint64_t bytes = 0;
+};
+
+namespace dj {
+
+// Descriptor of one solve for the cluster engine (64 bytes).
+struct SolveDesc {
+  const int32_t* W;
+  const int32_t* minout;
+  int32_t* dist;
+  int32_t* pred;
+  int64_t pitch;
+  int32_t n;
+  int32_t source;
+  uint32_t bits_u;
+  uint32_t span;
+  int32_t plain;
+  int32_t pad;
+};
+static_assert(sizeof(SolveDesc) == 64, "descriptor layout");
+
+struct DevCtx {
+  int device = -1;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  int coop = 0;
+  int cluster_launch = 0;
+  uint32_t* words = nullptr;  // device: [0] error bits, [1] phases of the last single solve
+};
+
+// error reporting (thread-local message)
+int set_error(int status, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+// per-device context of the current device (created on first use)
+int get_ctx(DevCtx** out);
+
+inline uint32_t host_bits_for(uint32_t n) {
+  uint32_t b = 1;
+  while (b < 31 && (1u << b) < n) ++b;
+  return b;
+}
+inline uint32_t host_span_for(uint32_t n) { return 1u << (32 - host_bits_for(n)); }
+
+SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, int plain);
+
+// engines (dj_solve.cu)
+int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
+                cudaStream_t st);
+struct ClusterLaunch {
+  int cluster_size = 8;
+  int threads = 256;
+  int clusters = 0;  // 0 = as many as fit
+};
+// Launch the cluster engine over k descriptors already on the device.
+// `queue` is a device word zeroed by this call before the launch.
+int launch_cluster(const SolveDesc* descs_dev, int32_t k, int32_t max_n, int32_t max_pitch, uint32_t* queue,
+                   const ClusterLaunch& cl, cudaStream_t st);
+// A cluster-engine launch resolved ahead of time: running it is one memset
+// and one kernel launch (both capturable in a CUDA graph).
+struct ClusterPlan {
+  void* fn = nullptr;
+  int clusters = 0;
+  int cluster_size = 0;
+  int threads = 0;
+  size_t smem = 0;
+  int swcap = 0;
+  int rgs_cap = 0;
+};
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan);
+int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st);
+int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters);
+bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl);
+
+}  // namespace dj

@@ -1,0 +1,323 @@
+// Graph construction: edge list (or dense matrix) -> device adjacency matrix.
+//
+// Section III of the paper: the input is an edge list that each program
+// writes into an n x n adjacency matrix (not timed); Section III-A: the -w
+// flag fills a directed graph, otherwise undirected.  Here the matrix is
+// built directly in HBM: a vectorised INF fill with a zero diagonal, a scatter
+// of the edges with atomicMin (so a repeated pair keeps its smallest weight,
+// independent of order), and one pass computing each row's smallest finite
+// off-diagonal weight (minout, used by the phase-batched solve).  Rows are
+// padded to a multiple of 32 int32 (128 bytes) with INF, the device analogue
+// of the paper's INF padding of Section III-B.
+#include <algorithm>
+#include <string>
+
+#include "dj_common.cuh"
+#include "dj_internal.h"
+
+namespace dj {
+
+__global__ void k_fill(int32_t* __restrict__ W, int64_t pitch, int32_t n) {
+  const int64_t nv = static_cast<int64_t>(n) * pitch / 4;
+  int4* W4 = reinterpret_cast<int4*>(W);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nv;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t e = i * 4;
+    const int64_t r = e / pitch;
+    const int64_t c = e - r * pitch;
+    int4 v = make_int4(int(kInf), int(kInf), int(kInf), int(kInf));
+    if (r >= c && r < c + 4) (&v.x)[r - c] = 0;
+    W4[i] = v;
+  }
+}
+
+__global__ void k_scatter(int32_t* __restrict__ W, int64_t pitch, const int32_t* __restrict__ src,
+                          const int32_t* __restrict__ dst, const int32_t* __restrict__ w, int64_t m,
+                          int directed) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t u = src[e], v = dst[e], x = w[e];
+    if (u == v) continue;  // self-loops ignored: the diagonal stays 0
+    atomicMin(W + static_cast<int64_t>(u) * pitch + v, x);
+    if (!directed) atomicMin(W + static_cast<int64_t>(v) * pitch + u, x);
+  }
+}
+
+// Copy a dense matrix with row stride ld into the padded layout, checking every
+// entry lies in [0, INF]; bad entries set flags[0].
+__global__ void k_copy_dense(int32_t* __restrict__ W, int64_t pitch, const int32_t* __restrict__ A, int64_t ld,
+                             int32_t n, uint32_t* flags) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < static_cast<int64_t>(n) * n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    const int32_t x = A[r * ld + c];
+    if (x < 0 && flags) atomicOr(flags, 1u);
+    W[r * pitch + c] = x;
+  }
+}
+
+// One warp per row: minout[u] = min finite W[u][v], v != u; plus the global
+// finite min / max (stats[0] = min, stats[1] = max).
+__global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n, int32_t* __restrict__ minout,
+                         uint32_t* stats) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  uint32_t gmin = kInf, gmax = 0;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t* row = W + u * pitch;
+    uint32_t mn = kInf, mx = 0;
+    for (int64_t v = lane; v < n; v += 32) {
+      const uint32_t x = static_cast<uint32_t>(row[v]);
+      if (v != u && x < kInf) {
+        mn = min(mn, x);
+        mx = max(mx, x);
+      }
+    }
+    mn = warp_min_u32(mn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) minout[u] = static_cast<int32_t>(mn);
+    gmin = min(gmin, mn);
+    gmax = max(gmax, mx);
+  }
+  if (lane == 0 && stats) {
+    atomicMin(stats, gmin);
+    atomicMax(stats + 1, gmax);
+  }
+}
+
+// Columns [n, pitch) of every row hold INF.
+__global__ void k_pad_cols(int32_t* __restrict__ W, int64_t pitch, int32_t n) {
+  const int64_t padw = pitch - n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < padw * n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / padw;
+    W[r * pitch + n + (i - r * padw)] = static_cast<int32_t>(kInf);
+  }
+}
+
+// flags[0] |= 1 if any of the n x n entries is negative.
+__global__ void k_check_nonneg(const int32_t* __restrict__ W, int64_t pitch, int32_t n, uint32_t* flags) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < static_cast<int64_t>(n) * n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / n;
+    if (W[r * pitch + (i - r * n)] < 0) atomicOr(flags, 1u);
+  }
+}
+
+}  // namespace dj
+
+using namespace dj;
+
+static int grid_for(int64_t work, int threads = 256) {
+  int64_t b = (work + threads - 1) / threads;
+  return static_cast<int>(std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32));
+}
+
+static int alloc_graph(int32_t n, int directed, dj_graph** out) {
+  auto* g = new dj_graph();
+  g->n = n;
+  g->pitch = (n + 31) / 32 * 32;
+  g->directed = directed ? 1 : 0;
+  cudaGetDevice(&g->device);
+  const size_t mbytes = static_cast<size_t>(n) * g->pitch * sizeof(int32_t);
+  cudaError_t e = cudaMalloc(&g->W, mbytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return set_error(DJ_ENOMEM, "cudaMalloc of the adjacency matrix failed (" + std::to_string(mbytes) + " bytes)");
+  }
+  e = cudaMalloc(&g->minout, static_cast<size_t>(n) * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->W);
+    delete g;
+    return set_error(DJ_ENOMEM, "cudaMalloc of the row minima failed");
+  }
+  g->bytes = mbytes + static_cast<size_t>(n) * sizeof(int32_t);
+  *out = g;
+  return DJ_OK;
+}
+
+// Row minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
+static int finish_graph(dj_graph* g, cudaStream_t st) {
+  uint32_t* stats = nullptr;
+  cudaError_t e = cudaMallocAsync(&stats, 2 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(stats)");
+  uint32_t init[2] = {kInf, 0};
+  cudaMemcpyAsync(stats, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
+  uint32_t res[2];
+  cudaMemcpyAsync(res, stats, sizeof(res), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(stats, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "building the row minima");
+  g->wmin = static_cast<int32_t>(res[0]);
+  g->wmax = static_cast<int32_t>(res[1]);
+  if (g->n > 1 && static_cast<int64_t>(g->n - 1) * g->wmax >= static_cast<int64_t>(DJ_INF))
+    return set_error(DJ_EOVERFLOW, "(n-1) * max weight >= INT32_MAX: path lengths could overflow int32");
+  return DJ_OK;
+}
+
+extern "C" int dj_load_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                             int directed, uint64_t stream, dj_graph** out) {
+  clear_error();
+  if (!out) return set_error(DJ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1) return set_error(DJ_EINVAL, "n must be >= 1");
+  if (m < 0) return set_error(DJ_EINVAL, "m must be >= 0");
+  if (m > 0 && (!src || !dst || !w)) return set_error(DJ_EINVAL, "edge arrays are NULL");
+  // host-side validation and the weight range of the kept (non-self-loop) edges
+  int64_t wmax = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    const int32_t u = src[e], v = dst[e], x = w[e];
+    if (u < 0 || u >= n || v < 0 || v >= n)
+      return set_error(DJ_EINVAL, "edge " + std::to_string(e) + " has a node id outside [0, n)");
+    if (x < 0 || x == DJ_INF)
+      return set_error(DJ_EINVAL, "edge " + std::to_string(e) + " has a weight outside [0, INT32_MAX)");
+    if (u != v && x > wmax) wmax = x;
+  }
+  if (n > 1 && static_cast<int64_t>(n - 1) * wmax >= static_cast<int64_t>(DJ_INF))
+    return set_error(DJ_EOVERFLOW, "(n-1) * max weight >= INT32_MAX: path lengths could overflow int32");
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  dj_graph* g = nullptr;
+  if (int rc = alloc_graph(n, directed, &g)) return rc;
+  k_fill<<<grid_for(static_cast<int64_t>(n) * g->pitch / 4), 256, 0, st>>>(g->W, g->pitch, n);
+  if (m > 0) {
+    const int64_t chunk = std::min<int64_t>(m, int64_t(1) << 24);  // 16 Mi edges (192 MiB) per stage
+    int32_t* stage = nullptr;
+    cudaError_t e = cudaMallocAsync(&stage, static_cast<size_t>(chunk) * 3 * sizeof(int32_t), st);
+    if (e != cudaSuccess) {
+      dj_graph_free(g);
+      return cuda_error(e, "cudaMallocAsync(edge staging)");
+    }
+    for (int64_t off = 0; off < m; off += chunk) {
+      const int64_t c = std::min(chunk, m - off);
+      cudaMemcpyAsync(stage, src + off, c * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(stage + chunk, dst + off, c * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(stage + 2 * chunk, w + off, c * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      k_scatter<<<grid_for(c), 256, 0, st>>>(g->W, g->pitch, stage, stage + chunk, stage + 2 * chunk, c, directed);
+      // the host arrays may be pageable: finish this stage before reusing the buffer
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        dj_graph_free(g);
+        return cuda_error(e, "scattering edges");
+      }
+    }
+    cudaFreeAsync(stage, st);
+  }
+  if (int rc = finish_graph(g, st)) {
+    dj_graph_free(g);
+    return rc;
+  }
+  *out = g;
+  return DJ_OK;
+}
+
+static int copy_dense_in(dj_graph* g, const int32_t* W, int64_t ld, int w_on_device, bool check, cudaStream_t st) {
+  const int32_t n = g->n;
+  uint32_t* flags = nullptr;
+  cudaError_t e;
+  if (check) {
+    e = cudaMallocAsync(&flags, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(flags)");
+    cudaMemsetAsync(flags, 0, sizeof(uint32_t), st);
+  }
+  if (w_on_device) {
+    k_copy_dense<<<grid_for(static_cast<int64_t>(n) * n), 256, 0, st>>>(g->W, g->pitch, W, ld, n,
+                                                                         flags ? flags : nullptr);
+  } else {
+    e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
+                          static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(n) * sizeof(int32_t),
+                          static_cast<size_t>(n), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(host matrix)");
+    if (check) k_check_nonneg<<<grid_for(static_cast<int64_t>(n) * n), 256, 0, st>>>(g->W, g->pitch, n, flags);
+  }
+  if (g->pitch > n)
+    k_pad_cols<<<grid_for(static_cast<int64_t>(g->pitch - n) * n), 256, 0, st>>>(g->W, g->pitch, n);
+  if (!check) return DJ_OK;
+  uint32_t bad = 0;
+  cudaMemcpyAsync(&bad, flags, sizeof(bad), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(flags, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "copying the dense matrix");
+  if (bad) return set_error(DJ_EINVAL, "matrix holds a negative entry");
+  return DJ_OK;
+}
+
+extern "C" int dj_load_dense(int32_t n, const int32_t* W, int64_t ld, int w_on_device, uint64_t stream,
+                             dj_graph** out) {
+  clear_error();
+  if (!out) return set_error(DJ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !W || ld < n) return set_error(DJ_EINVAL, "need n >= 1, W != NULL and ld >= n");
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  dj_graph* g = nullptr;
+  if (int rc = alloc_graph(n, 1, &g)) return rc;
+  if (int rc = copy_dense_in(g, W, ld, w_on_device, true, st)) {
+    dj_graph_free(g);
+    return rc;
+  }
+  if (int rc = finish_graph(g, st)) {
+    dj_graph_free(g);
+    return rc;
+  }
+  *out = g;
+  return DJ_OK;
+}
+
+extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64_t stream) {
+  clear_error();
+  if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
+                                    static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
+                                    static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(upload)");
+  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "row minima");
+  return DJ_OK;
+}
+
+extern "C" int dj_graph_download(const dj_graph* g, int32_t* W, int64_t ld, uint64_t stream) {
+  clear_error();
+  if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpy2DAsync(W, static_cast<size_t>(ld) * sizeof(int32_t), g->W,
+                                    static_cast<size_t>(g->pitch) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
+                                    static_cast<size_t>(g->n), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(download)");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "download");
+  return DJ_OK;
+}
+
+extern "C" int dj_graph_get_info(const dj_graph* g, dj_graph_info* info) {
+  clear_error();
+  if (!g || !info) return set_error(DJ_EINVAL, "NULL argument");
+  info->n = g->n;
+  info->pitch = g->pitch;
+  info->directed = g->directed;
+  info->min_weight = g->wmin;
+  info->max_weight = g->wmax;
+  info->device = g->device;
+  info->matrix = g->W;
+  info->minout = g->minout;
+  info->bytes = g->bytes;
+  return DJ_OK;
+}
+
+extern "C" int dj_graph_free(dj_graph* g) {
+  clear_error();
+  if (!g) return DJ_OK;
+  cudaFree(g->W);
+  cudaFree(g->minout);
+  delete g;
+  return DJ_OK;
+}

@@ -1,0 +1,553 @@
+// Solve engines for Algorithm 1 (Section III-A), both persistent:
+//
+//  * Grid engine: one cooperative launch with every SM's CTA(s) resident.  Each
+//    CTA owns a contiguous column slice (its nodes' dist / pred / visited /
+//    minout live in its shared memory for the whole solve); the only global
+//    traffic besides the matrix rows is one 16-byte partial per CTA and the
+//    candidate list per phase, exchanged through L2 around ONE grid barrier per
+//    phase.  This is the in-kernel form of the paper's MPI Allreduce step
+//    (Algorithm 2, Section III-B), with the 1-D column partition of
+//    Section III-B applied to CTAs instead of processes.
+//
+//  * Cluster engine: one thread-block cluster per solve; the slices live in
+//    the cluster's distributed shared memory and the per-phase exchange is a
+//    DSMEM read of the other CTAs' partials and candidate lists around one
+//    cluster barrier.  Clusters pull solves from a device queue, so one launch
+//    runs many solves (batches, serving) and small single solves.
+//
+// The phase logic (what is settled per pass and why it equals Algorithm 1) is
+// in dj_core.cuh.
+#include <algorithm>
+#include <string>
+
+#include "dj_common.cuh"
+#include "dj_core.cuh"
+#include "dj_internal.h"
+
+namespace dj {
+
+// ============================================================ grid engine
+
+struct GridParams {
+  const int32_t* W;
+  const int32_t* minout;
+  int32_t* dist_out;
+  int32_t* pred_out;
+  uint32_t* ctl;  // [0] barrier arrivals, [1..3] candidate counters, [5] abort flag
+  uint4* partials;  // [2][G]: (key lo, key hi, L_c, count)
+  uint2* cand;      // [2][cand_cap]
+  uint32_t* words;  // per-device words: [0] error bits, [1] phases
+  int64_t pitch;
+  int64_t timeout_ns;
+  int32_t n;
+  int32_t nvec_total;
+  int32_t source;
+  int32_t plain;
+  uint32_t bits_u;
+  uint32_t span;
+  uint32_t cand_cap;
+  int32_t swcap;
+  int32_t rgs_cap;
+  int32_t skip_cta;
+};
+
+// Grid-wide barrier on a monotonic arrival counter (zeroed before launch).
+// Bounded: after timeout_ns it records kErrTimeout, raises the launch's abort
+// flag and returns false; CTAs already waiting see the flag and leave too.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uint32_t* abort_flag, uint32_t* err,
+                                             int64_t timeout_ns, uint32_t* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_add_release_gpu(bar, 1u);
+    uint32_t ok = 1;
+    if (static_cast<int32_t>(ld_acquire_gpu(bar) - target) < 0) {
+      const uint64_t t0 = global_ns();
+      uint32_t spins = 0;
+      while (static_cast<int32_t>(ld_acquire_gpu(bar) - target) < 0) {
+        if ((++spins & 63u) == 0) {
+          if (ld_relaxed_gpu(abort_flag)) {
+            ok = 0;
+            break;
+          }
+          if (static_cast<int64_t>(global_ns() - t0) > timeout_ns) {
+            atomicOr(err, kErrTimeout);
+            atomicExch(abort_flag, 1u);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+template <int V, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ BlockScratch sc;
+  __shared__ Decision s_dec;
+  __shared__ uint32_t s_word;
+  __shared__ uint32_t s_flag;
+
+  const int G = gridDim.x, b = blockIdx.x;
+  Slice s;
+  const int v0 = static_cast<int>(static_cast<int64_t>(b) * p.nvec_total / G);
+  const int v1 = static_cast<int>(static_cast<int64_t>(b + 1) * p.nvec_total / G);
+  s.c0 = 4 * v0;
+  s.nvec = v1 - v0;
+  s.sw = 4 * s.nvec;
+  uint8_t* q = smem;
+  uint64_t* merge = reinterpret_cast<uint64_t*>(q);
+  q += static_cast<size_t>(p.rgs_cap) * p.swcap * 8;
+  uint2* own = reinterpret_cast<uint2*>(q);
+  q += static_cast<size_t>(p.swcap) * 8;
+  s.dist = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.pred = reinterpret_cast<int32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.minout = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.vis = q;
+
+  slice_init(s, p.n, p.source, p.minout, !p.plain);
+  const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
+  __syncthreads();
+
+  uint32_t* bar = p.ctl;
+  uint32_t* cnt = p.ctl + 1;
+  uint32_t* abort_flag = p.ctl + 5;
+  uint32_t phase = 0;
+  for (;;) {
+    // 1. publish this slice's partial and candidates
+    uint64_t key;
+    uint32_t Lc;
+    const int c = slice_publish(s, p.span, p.plain != 0, own, &key, &Lc, &sc);
+    if (threadIdx.x == 0) {
+      s_word = (c && !p.plain) ? atomicAdd(&cnt[phase % 3], static_cast<uint32_t>(c)) : 0u;
+      p.partials[static_cast<size_t>(phase & 1) * G + b] =
+          make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
+    }
+    __syncthreads();
+    if (!p.plain) {
+      uint2* dst = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap + s_word;
+      for (int i = threadIdx.x; i < c; i += blockDim.x) dst[i] = own[i];
+    }
+    // 2. one grid barrier per phase
+    if (b == p.skip_cta) return;  // testing: this CTA never arrives
+    if (!grid_barrier(bar, (phase + 1) * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag))
+      return;
+    // 3. global decision from the G partials
+    if (threadIdx.x < 32) {
+      uint64_t k = kNoKey;
+      uint32_t l = 0xFFFFFFFFu;
+      const uint4* part = p.partials + static_cast<size_t>(phase & 1) * G;
+      for (int i = threadIdx.x; i < G; i += 32) {
+        const uint4 x = __ldcg(part + i);
+        const uint64_t kk = (static_cast<uint64_t>(x.y) << 32) | x.x;
+        k = kk < k ? kk : k;
+        l = min(l, x.z);
+      }
+      k = warp_min_u64(k);
+      l = warp_min_u32(l);
+      if (threadIdx.x == 0) {
+        s_dec = make_decision(k, l, p.span, p.plain != 0);
+        s_word = p.plain ? 1u : __ldcg(&cnt[phase % 3]);
+        if (b == 0) cnt[(phase + 2) % 3] = 0;  // slot of phase+2's publication, last read in phase-1
+      }
+    }
+    __syncthreads();
+    const Decision D = s_dec;
+    const int total = static_cast<int>(s_word);
+    if (D.m >= kInf) break;
+    slice_mark(s, D);
+    // 4. fused relaxation of the settled rows over this slice
+    uint64_t best[V][4];
+    best_reset<V>(best);
+    if (p.plain) {
+      const uint2 one = make_uint2(D.a, D.m);
+      relax_entries<V, U>([one](int) { return one; }, 1, s, t, p.W, p.pitch, D, p.bits_u, best);
+    } else {
+      const uint2* list = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap;
+      relax_entries<V, U>([list](int i) { return __ldcg(list + i); }, total, s, t, p.W, p.pitch, D, p.bits_u,
+                          best);
+    }
+    merge_commit<V>(s, t, merge, p.bits_u, best);
+    ++phase;
+  }
+  slice_write_out(s, p.n, p.dist_out, p.pred_out);
+  if (b == 0 && threadIdx.x == 0) p.words[1] = phase;
+}
+
+// ============================================================ cluster engine
+
+struct ClusterParams {
+  const SolveDesc* descs;
+  uint32_t* queue;  // [0] next solve index (zeroed before launch)
+  int32_t k;
+  int32_t swcap;
+  int32_t rgs_cap;
+};
+
+template <int V, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ BlockScratch sc;
+  __shared__ __align__(16) uint4 s_part[2];  // this CTA's published partial, per phase parity
+  __shared__ uint32_t s_job;                 // rank 0: the solve index it fetched
+  __shared__ uint32_t s_jobl;                // local copy
+  __shared__ Decision s_dec;
+  __shared__ uint32_t s_off[17];   // candidate offsets of the ranks (prefix)
+  __shared__ uint32_t s_addr[16];  // DSMEM address of each rank's candidate list
+
+  const uint32_t rank = cluster_rank(), C = cluster_size();
+  uint8_t* q = smem;
+  uint64_t* merge = reinterpret_cast<uint64_t*>(q);
+  q += static_cast<size_t>(p.rgs_cap) * p.swcap * 8;
+  uint2* own = reinterpret_cast<uint2*>(q);  // [2][swcap]
+  q += static_cast<size_t>(p.swcap) * 16;
+  Slice s;
+  s.dist = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.pred = reinterpret_cast<int32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.minout = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.vis = q;
+
+  for (;;) {
+    // next solve: rank 0 takes it from the queue, every CTA reads it through DSMEM
+    if (rank == 0 && threadIdx.x == 0) s_job = atomicAdd(p.queue, 1u);
+    cluster_sync_all();
+    if (threadIdx.x == 0) s_jobl = (rank == 0) ? s_job : ld_dsmem_u32(dsmem_addr(&s_job, 0));
+    __syncthreads();
+    const uint32_t job = s_jobl;
+    if (job >= static_cast<uint32_t>(p.k)) {
+      cluster_sync_all();  // rank 0's s_job stays readable until everyone has it
+      return;
+    }
+    const SolveDesc d = p.descs[job];
+    const int nvec_total = static_cast<int>(d.pitch / 4);
+    const int v0 = static_cast<int>(static_cast<int64_t>(rank) * nvec_total / C);
+    const int v1 = static_cast<int>(static_cast<int64_t>(rank + 1) * nvec_total / C);
+    s.c0 = 4 * v0;
+    s.nvec = v1 - v0;
+    s.sw = 4 * s.nvec;
+    slice_init(s, d.n, d.source, d.minout, !d.plain);
+    const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
+    __syncthreads();
+
+    uint32_t phase = 0;
+    for (;;) {
+      uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
+      uint64_t key;
+      uint32_t Lc;
+      const int c = slice_publish(s, d.span, d.plain != 0, mine, &key, &Lc, &sc);
+      if (threadIdx.x == 0)
+        s_part[phase & 1] =
+            make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
+      cluster_sync_all();
+      if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
+        if (lane < C) x = ld_dsmem_u32x4(dsmem_addr(&s_part[phase & 1], lane));
+        uint64_t k = (static_cast<uint64_t>(x.y) << 32) | x.x;
+        uint32_t l = x.z;
+        k = warp_min_u64(k);
+        l = warp_min_u32(l);
+        const Decision D = make_decision(k, l, d.span, d.plain != 0);
+        // in plain mode only the argmin row is relaxed: keep the argmin owner's list
+        const uint32_t cntv = x.w;
+        uint32_t incl = cntv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= static_cast<uint32_t>(o)) incl += tt;
+        }
+        if (lane < C) {
+          s_off[lane] = incl - cntv;
+          s_addr[lane] = dsmem_addr(own + static_cast<size_t>(phase & 1) * p.swcap, lane);
+        }
+        if (lane == C - 1) s_off[C] = incl;
+        if (lane == 0) s_dec = D;
+      }
+      __syncthreads();
+      const Decision D = s_dec;
+      if (D.m >= kInf) break;
+      slice_mark(s, D);
+      uint64_t best[V][4];
+      best_reset<V>(best);
+      const int total = static_cast<int>(s_off[C]);
+      const int Cn = static_cast<int>(C);
+      relax_entries<V, U>(
+          [Cn](int i) {
+            int r = 0;
+#pragma unroll
+            for (int st = 8; st >= 1; st >>= 1)
+              if (r + st < Cn && static_cast<int>(s_off[r + st]) <= i) r += st;
+            return ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
+          },
+          total, s, t, d.W, d.pitch, D, d.bits_u, best);
+      merge_commit<V>(s, t, merge, d.bits_u, best);
+      ++phase;
+    }
+    slice_write_out(s, d.n, d.dist, d.pred);
+  }
+}
+
+// ============================================================ host launchers
+
+namespace {
+
+template <int V>
+struct UFor {
+  static constexpr int value = V == 1 ? 8 : (V == 2 ? 4 : 2);
+};
+
+constexpr int kGridThreads = 512;
+constexpr int kClusterThreads = 256;
+
+size_t grid_smem(int swcap, int rgs_cap) {
+  return static_cast<size_t>(rgs_cap) * swcap * 8 + static_cast<size_t>(swcap) * (8 + 12 + 1) + 16;
+}
+size_t cluster_smem(int swcap, int rgs_cap) {
+  return static_cast<size_t>(rgs_cap) * swcap * 8 + static_cast<size_t>(swcap) * (16 + 12 + 1) + 16;
+}
+
+// smallest V in {1, 2, 4} whose column chunks fit the warps (at least one row group)
+int pick_v(int nvec_cta, int nwarps) {
+  for (int v : {1, 2, 4})
+    if ((nvec_cta + 32 * v - 1) / (32 * v) <= nwarps) return v;
+  return 0;
+}
+
+template <int V>
+void* grid_kernel() {
+  return reinterpret_cast<void*>(&k_sssp_grid<V, UFor<V>::value, kGridThreads>);
+}
+template <int V>
+void* cluster_kernel() {
+  return reinterpret_cast<void*>(&k_sssp_cluster<V, UFor<V>::value, kClusterThreads>);
+}
+void* grid_kernel_for(int v) {
+  switch (v) {
+    case 1: return grid_kernel<1>();
+    case 2: return grid_kernel<2>();
+    case 4: return grid_kernel<4>();
+  }
+  return nullptr;
+}
+void* cluster_kernel_for(int v) {
+  switch (v) {
+    case 1: return cluster_kernel<1>();
+    case 2: return cluster_kernel<2>();
+    case 4: return cluster_kernel<4>();
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
+                cudaStream_t st) {
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  if (!ctx->coop) return set_error(DJ_EUNSUPPORTED, "device lacks cooperative launch");
+  const int nvec_total = g->pitch / 4;
+  const int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
+  int G = std::min(ctx->num_sms * per_sm, nvec_total);
+  const int nwarps = kGridThreads / 32;
+  int nvec_cta = (nvec_total + G - 1) / G;
+  const int V = pick_v(nvec_cta, nwarps);
+  if (!V) return set_error(DJ_EUNSUPPORTED, "graph too large for the grid engine");
+  const int swcap = 4 * nvec_cta;
+  const int wpr = (nvec_cta + 32 * V - 1) / (32 * V);
+  int rgs_cap = nwarps / wpr;
+  while (rgs_cap > 1 && grid_smem(swcap, rgs_cap) > static_cast<size_t>(ctx->max_smem_optin) - 4096) --rgs_cap;
+  const size_t smem = grid_smem(swcap, rgs_cap);
+  if (smem > static_cast<size_t>(ctx->max_smem_optin)) return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
+  void* fn = grid_kernel_for(V);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, smem);
+  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (occ < 1) return set_error(DJ_EUNSUPPORTED, "grid engine cannot be resident");
+  if (occ < per_sm) G = std::min(ctx->num_sms * occ, nvec_total);
+
+  const size_t ctl_bytes = 256;
+  const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
+  const uint32_t cand_cap = static_cast<uint32_t>(g->pitch);
+  const size_t cand_bytes = static_cast<size_t>(2) * cand_cap * sizeof(uint2);
+  uint8_t* ws = nullptr;
+  e = cudaMallocAsync(&ws, ctl_bytes + part_bytes + cand_bytes, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(grid workspace)");
+  cudaMemsetAsync(ws, 0, ctl_bytes, st);
+
+  GridParams p;
+  p.W = g->W;
+  p.minout = g->minout;
+  p.dist_out = dist;
+  p.pred_out = pred;
+  p.ctl = reinterpret_cast<uint32_t*>(ws);
+  p.partials = reinterpret_cast<uint4*>(ws + ctl_bytes);
+  p.cand = reinterpret_cast<uint2*>(ws + ctl_bytes + part_bytes);
+  p.words = ctx->words;
+  p.pitch = g->pitch;
+  p.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
+  p.n = g->n;
+  p.nvec_total = nvec_total;
+  p.source = source;
+  p.plain = o.mode == DJ_MODE_PLAIN ? 1 : 0;
+  p.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
+  p.span = host_span_for(static_cast<uint32_t>(g->n));
+  p.cand_cap = cand_cap;
+  p.swcap = swcap;
+  p.rgs_cap = rgs_cap;
+  p.skip_cta = o.debug_skip_cta;
+  void* args[] = {&p};
+  e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, smem, st);
+  cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
+  return DJ_OK;
+}
+
+static int cluster_dims(int32_t max_pitch, const ClusterLaunch& cl, int* V, int* swcap, int* rgs_cap, size_t* smem) {
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  const int C = cl.cluster_size;
+  const int nvec_total = max_pitch / 4;
+  const int nvec_cta = (nvec_total + C - 1) / C;
+  const int nwarps = kClusterThreads / 32;
+  *V = pick_v(nvec_cta, nwarps);
+  if (!*V) return set_error(DJ_EUNSUPPORTED, "graph too large for this cluster size");
+  *swcap = 4 * std::max(nvec_cta, 1);
+  const int wpr = (nvec_cta + 32 * *V - 1) / (32 * *V);
+  *rgs_cap = std::max(1, nwarps / std::max(wpr, 1));
+  while (*rgs_cap > 1 && cluster_smem(*swcap, *rgs_cap) > static_cast<size_t>(ctx->max_smem_optin) - 4096) --*rgs_cap;
+  *smem = cluster_smem(*swcap, *rgs_cap);
+  if (*smem > static_cast<size_t>(ctx->max_smem_optin))
+    return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory for this cluster size");
+  return DJ_OK;
+}
+
+static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(cluster smem)");
+  if (cl.cluster_size > 8) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return cuda_error(e, "non-portable cluster size");
+  }
+  return DJ_OK;
+}
+
+int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters) {
+  int V, swcap, rgs_cap;
+  size_t smem;
+  if (int rc = cluster_dims(max_pitch, cl, &V, &swcap, &rgs_cap, &smem)) return rc;
+  void* fn = cluster_kernel_for(V);
+  if (int rc = prepare_cluster(fn, cl, smem)) return rc;
+  cudaLaunchConfig_t cfg = {};
+  DevCtx* ctx = nullptr;
+  get_ctx(&ctx);
+  cfg.gridDim = dim3(cl.cluster_size * ctx->num_sms);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl.cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveClusters");
+  if (n < 1) return set_error(DJ_EUNSUPPORTED, "cluster configuration cannot be resident");
+  *clusters = n;
+  return DJ_OK;
+}
+
+bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl) {
+  int n = 0;
+  const bool ok = cluster_max_clusters(max_pitch, cl, &n) == DJ_OK && n >= 1;
+  if (!ok) clear_error();
+  return ok;
+}
+
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan) {
+  if (cl.cluster_size < 1 || cl.cluster_size > 16) return set_error(DJ_EINVAL, "cluster size must be 1..16");
+  int V, swcap, rgs_cap;
+  size_t smem;
+  if (int rc = cluster_dims(max_pitch, cl, &V, &swcap, &rgs_cap, &smem)) return rc;
+  void* fn = cluster_kernel_for(V);
+  if (int rc = prepare_cluster(fn, cl, smem)) return rc;
+  int Q = cl.clusters;
+  if (Q <= 0) {
+    if (int rc = cluster_max_clusters(max_pitch, cl, &Q)) return rc;
+  }
+  plan->fn = fn;
+  plan->clusters = std::max(1, std::min(Q, std::max(k, 1)));
+  plan->cluster_size = cl.cluster_size;
+  plan->threads = kClusterThreads;
+  plan->smem = smem;
+  plan->swcap = swcap;
+  plan->rgs_cap = rgs_cap;
+  return DJ_OK;
+}
+
+int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(queue)");
+  ClusterParams p;
+  p.descs = descs_dev;
+  p.queue = queue;
+  p.k = k;
+  p.swcap = plan.swcap;
+  p.rgs_cap = plan.rgs_cap;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(plan.clusters * plan.cluster_size));
+  cfg.blockDim = dim3(static_cast<unsigned>(plan.threads));
+  cfg.dynamicSmemBytes = plan.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = plan.cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {&p};
+  e = cudaLaunchKernelExC(&cfg, plan.fn, args);
+  if (e != cudaSuccess) return cuda_error(e, "cudaLaunchKernelEx(cluster engine)");
+  return DJ_OK;
+}
+
+int launch_cluster(const SolveDesc* descs_dev, int32_t k, int32_t /*max_n*/, int32_t max_pitch, uint32_t* queue,
+                   const ClusterLaunch& cl, cudaStream_t st) {
+  ClusterPlan plan;
+  if (int rc = plan_cluster(max_pitch, cl, k, &plan)) return rc;
+  return run_cluster(plan, descs_dev, k, queue, st);
+}
+
+SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, int plain) {
+  SolveDesc d;
+  d.W = g->W;
+  d.minout = g->minout;
+  d.dist = dist;
+  d.pred = pred;
+  d.pitch = g->pitch;
+  d.n = g->n;
+  d.source = source;
+  d.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
+  d.span = host_span_for(static_cast<uint32_t>(g->n));
+  d.plain = plain;
+  d.pad = 0;
+  return d;
+}
+
+}  // namespace dj

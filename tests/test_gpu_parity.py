@@ -1,0 +1,297 @@
+"""GPU parity: dist and pred from the CUDA path equal the CPU oracle bit for bit.
+
+All arithmetic is int32, so the tolerance is zero: every element must match.
+Inputs are the paper's worked matrices and padded example, seeded synthetic
+graphs at ragged sizes (spanning several CTA slices and a partial last tile),
+tie-heavy and zero-weight graphs, weights at the int32 overflow limit, and the
+full-size dense and sparse workloads.  Every call goes through the C ABI.
+"""
+import numpy as np
+import pytest
+
+import _pins as P
+import graphgen
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = [("grid", 1), ("cluster", 2)]
+MODES = [("phase", 1), ("plain", 2)]
+
+
+@pytest.fixture(scope="module")
+def dj():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_03667_gb300 import dj as _dj
+    torch.cuda.set_device(0)
+    return _dj
+
+
+def solve(dj, g, s, engine=0, mode=0, cluster_size=0):
+    import torch
+    n = dj.dj_graph_get_info(g)["n"]
+    dist = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+    pred = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+    dj.dj_sssp_ex(g, s, dist, pred, dj.make_solve_opts(mode=mode, engine=engine, cluster_size=cluster_size))
+    dj.dj_sync()
+    return dist.cpu().numpy(), pred.cpu().numpy()
+
+
+def assert_same(got, ref, what=""):
+    d, p = got
+    dr, pr = ref
+    if not np.array_equal(d, dr):
+        bad = np.nonzero(d != dr)[0]
+        raise AssertionError(f"{what}: dist differs at {bad.size} nodes, first {bad[:5]}: {d[bad[:5]]} vs {dr[bad[:5]]}")
+    if not np.array_equal(p, pr):
+        bad = np.nonzero(p != pr)[0]
+        raise AssertionError(f"{what}: pred differs at {bad.size} nodes, first {bad[:5]}: {p[bad[:5]]} vs {pr[bad[:5]]}")
+
+
+@pytest.mark.parametrize("engine", [e for _, e in ENGINES], ids=[n for n, _ in ENGINES])
+@pytest.mark.parametrize("mode", [m for _, m in MODES], ids=[n for n, _ in MODES])
+def test_worked_matrices(dj, engine, mode):
+    g = P.parse_golden("worked_4node.txt")
+    e = g["edges"]
+    for kind, directed in (("undirected", False), ("directed", True)):
+        G = dj.dj_load_edges(4, e[:, 0], e[:, 1], e[:, 2], directed)
+        assert np.array_equal(dj.dj_graph_download(G), g["matrices"][kind])
+        for k, s, dist, pred in g["expect"]:
+            if k == kind:
+                assert_same(solve(dj, G, s, engine, mode), (dist, pred), f"{kind} s={s}")
+        G.free()
+
+
+@pytest.mark.parametrize("engine", [e for _, e in ENGINES], ids=[n for n, _ in ENGINES])
+def test_padded_example_dense_load(dj, engine):
+    g = P.parse_golden("padded_6node.txt")
+    G = dj.dj_load_dense(g["matrices"]["padded"])
+    for _, s, dist, pred in g["expect"]:
+        assert_same(solve(dj, G, s, engine), (dist, pred), f"padded s={s}")
+
+
+@pytest.mark.parametrize("engine", [e for _, e in ENGINES], ids=[n for n, _ in ENGINES])
+@pytest.mark.parametrize("mode", [m for _, m in MODES], ids=[n for n, _ in MODES])
+def test_dense_n1024(dj, orc, engine, mode):
+    spec = graphgen.WORKLOADS["dense_n1024_p0.1"]
+    e = graphgen.make_graph(spec)
+    s = graphgen.workload_source(spec)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+    assert np.array_equal(dj.dj_graph_download(G), W)
+    ref = orc.dijkstra(W, s)
+    assert_same(solve(dj, G, s, engine, mode), ref, "n=1024")
+    for s2 in (1, 511, 1023):
+        assert_same(solve(dj, G, s2, engine, mode), orc.dijkstra(W, s2), f"n=1024 s={s2}")
+
+
+RAGGED = [1, 2, 3, 5, 31, 33, 64, 97, 255, 1000, 1025, 2047, 4099, 5003]
+
+
+@pytest.mark.parametrize("n", RAGGED)
+def test_ragged_sizes_ties_and_unreachable(dj, orc, n):
+    rng = np.random.default_rng(n)
+    for directed in (False, True):
+        m = int(min(n * (n - 1) // 2, 6 * n))
+        e = graphgen.random_edges(n, m, 1, 3, seed=1000 + n + int(directed), directed=directed)  # heavy ties
+        G = dj.dj_load_edges(n, e.src, e.dst, e.w, directed)
+        W = orc.build_matrix(n, e.src, e.dst, e.w, directed)
+        srcs = sorted({0, n - 1, int(rng.integers(0, n))})
+        for s in srcs:
+            ref = orc.dijkstra(W, s)
+            for ename, engine in ENGINES:
+                for mname, mode in MODES:
+                    if mode == 2 and n > 1100:
+                        continue
+                    assert_same(solve(dj, G, s, engine, mode), ref, f"n={n} {ename}/{mname} directed={directed} s={s}")
+        G.free()
+
+
+@pytest.mark.parametrize("cluster_size", [1, 2, 4, 8, 16])
+def test_cluster_sizes(dj, orc, cluster_size):
+    e = graphgen.bernoulli(3001, 0.02, 1, 50, seed=77)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    assert_same(solve(dj, G, 123, 2, 1, cluster_size), orc.dijkstra(W, 123), f"C={cluster_size}")
+
+
+def test_zero_weights(dj, orc):
+    for n, seed in ((40, 1), (700, 2), (5000, 3)):
+        e = graphgen.random_edges(n, 5 * n, 0, 2, seed=seed, directed=bool(seed % 2))
+        G = dj.dj_load_edges(n, e.src, e.dst, e.w, e.directed)
+        W = orc.build_matrix(n, e.src, e.dst, e.w, e.directed)
+        assert dj.dj_graph_get_info(G)["min_weight"] == 0
+        for s in (0, n // 2):
+            ref = orc.dijkstra(W, s)
+            for _, engine in ENGINES:
+                assert_same(solve(dj, G, s, engine), ref, f"zero weights n={n} s={s}")
+
+
+def test_weights_at_overflow_limit(dj, orc):
+    """Large weights shrink the packing span: the capped settle bound must stay exact."""
+    n = 3000
+    wmax = (2**31 - 2) // (n - 1)
+    e = graphgen.random_edges(n, 8 * n, wmax // 2, wmax, seed=5, directed=True)
+    G = dj.dj_load_edges(n, e.src, e.dst, e.w, True)
+    W = orc.build_matrix(n, e.src, e.dst, e.w, True)
+    for s in (0, 1234):
+        ref = orc.dijkstra(W, s)
+        for _, engine in ENGINES:
+            assert_same(solve(dj, G, s, engine), ref, f"near-overflow s={s}")
+
+
+def test_complete_equal_weights_and_path(dj, orc):
+    n = 2000
+    W = np.full((n, n), 9, dtype=np.int32)
+    np.fill_diagonal(W, 0)
+    G = dj.dj_load_dense(W)
+    d, p = solve(dj, G, 7)
+    assert (np.delete(d, 7) == 9).all() and (np.delete(p, 7) == 7).all() and d[7] == 0 and p[7] == -1
+    src = np.arange(n - 1, dtype=np.int32)
+    G2 = dj.dj_load_edges(n, src, src + 1, np.full(n - 1, 3, dtype=np.int32), True)
+    d, p = solve(dj, G2, 0)
+    assert np.array_equal(d, 3 * np.arange(n)) and np.array_equal(p, np.arange(n) - 1)
+
+
+def test_dense_n16384_full(dj, orc):
+    spec = graphgen.WORKLOADS["dense_n16384_p0.5"]
+    e = graphgen.make_graph(spec)
+    s = graphgen.workload_source(spec)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+    ref = orc.dijkstra(W, s)
+    got = solve(dj, G, s)  # the engine and launch the benchmark times
+    assert_same(got, ref, "n=16384 p=0.5")
+    assert P.check_invariants(W, s, *got) == []
+    assert dj.dj_last_phases() > 0
+
+
+def test_sparse_directed_n32768_full(dj, orc):
+    spec = graphgen.WORKLOADS["sparse_directed_n32768_deg8"]
+    e = graphgen.make_graph(spec)
+    s = graphgen.workload_source(spec)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+    ref = orc.dijkstra(W, s)
+    assert_same(solve(dj, G, s), ref, "n=32768 directed")
+    assert_same(solve(dj, G, s, engine=2, cluster_size=16), ref, "n=32768 directed, cluster engine")
+
+
+def test_batch_matches_single_and_oracle(dj, orc):
+    import torch
+    spec = graphgen.WORKLOADS["multisource_n8192_p0.05_k256"]
+    e = graphgen.make_graph(spec)
+    srcs = graphgen.sources(e.n, spec["k"], spec["seed"])
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+    k = len(srcs)
+    D = torch.full((k, e.n), -5, dtype=torch.int32, device="cuda")
+    Pr = torch.full((k, e.n), -5, dtype=torch.int32, device="cuda")
+    dj.dj_sssp_batch([G] * k, srcs, list(D), list(Pr))
+    dj.dj_sync()
+    D, Pr = D.cpu().numpy(), Pr.cpu().numpy()
+    for i in range(0, k, 8):  # oracle on a seeded sample of the sources
+        assert_same((D[i], Pr[i]), orc.dijkstra(W, int(srcs[i])), f"batch source #{i}")
+    for i in range(1, k, 8):  # alone vs in the mix
+        assert_same((D[i], Pr[i]), solve(dj, G, int(srcs[i])), f"batch vs single #{i}")
+
+
+def test_batch_uneven_graphs(dj, orc):
+    import torch
+    sizes = [5000, 33, 1, 1024, 2999, 64, 7000, 300]
+    graphs, Ws, srcs, dists, preds = [], [], [], [], []
+    for i, n in enumerate(sizes):
+        e = graphgen.bernoulli(n, min(1.0, 20.0 / max(n, 1)), 1, 100, seed=900 + i)
+        graphs.append(dj.dj_load_edges(n, e.src, e.dst, e.w, False))
+        Ws.append(orc.build_matrix(n, e.src, e.dst, e.w, False))
+        srcs.append((7 * i) % n)
+        dists.append(torch.full((n,), -5, dtype=torch.int32, device="cuda"))
+        preds.append(torch.full((n,), -5, dtype=torch.int32, device="cuda"))
+    for mode in (1, 2):
+        b = dj.dj_batch_create(graphs, srcs, dists, preds, mode=mode)
+        dj.dj_batch_launch(b)
+        dj.dj_sync()
+        for i in range(len(sizes)):
+            assert_same((dists[i].cpu().numpy(), preds[i].cpu().numpy()), orc.dijkstra(Ws[i], srcs[i]),
+                        f"uneven batch #{i} n={sizes[i]} mode={mode}")
+        b.free()
+
+
+def test_batch_in_cuda_graph(dj, orc):
+    import torch
+    e = graphgen.bernoulli(4000, 0.05, 1, 1000, seed=31)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    srcs = graphgen.sources(e.n, 12, 31)
+    D = torch.full((12, e.n), -5, dtype=torch.int32, device="cuda")
+    Pr = torch.full((12, e.n), -5, dtype=torch.int32, device="cuda")
+    b = dj.dj_batch_create([G] * 12, srcs, list(D), list(Pr))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dj.dj_batch_launch(b, s)  # warm-up outside capture
+    s.synchronize()
+    D.fill_(-5)
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=s):
+        dj.dj_batch_launch(b, s)
+    cg.replay()
+    cg.replay()
+    torch.cuda.synchronize()
+    for i in range(12):
+        assert_same((D[i].cpu().numpy(), Pr[i].cpu().numpy()), orc.dijkstra(W, int(srcs[i])), f"graph replay #{i}")
+
+
+def test_argument_errors(dj):
+    import torch
+    one = np.array([0], dtype=np.int32)
+    with pytest.raises(dj.DjError) as ei:
+        dj.dj_load_edges(2, one, np.array([2], dtype=np.int32), one, False)
+    assert ei.value.status == dj.DJ_EINVAL
+    with pytest.raises(dj.DjError) as ei:
+        dj.dj_load_edges(2, one, one + 1, np.array([-3], dtype=np.int32), False)
+    assert ei.value.status == dj.DJ_EINVAL
+    with pytest.raises(dj.DjError) as ei:
+        dj.dj_load_edges(3, one, one + 1, np.array([2**30], dtype=np.int32), False)
+    assert ei.value.status == dj.DJ_EOVERFLOW
+    G = dj.dj_load_edges(3, one, one + 1, np.array([5], dtype=np.int32), False)
+    d = torch.empty(3, dtype=torch.int32, device="cuda")
+    with pytest.raises(dj.DjError) as ei:
+        dj.dj_sssp(G, 3, d, d.clone())
+    assert ei.value.status == dj.DJ_EINVAL
+    with pytest.raises(dj.DjError):
+        dj.dj_load_dense(np.array([[0, -1], [1, 0]], dtype=np.int32))
+
+
+def test_bounded_barrier_timeout_reports_and_recovers(dj, orc):
+    """One CTA never arrives at the first grid barrier: the others give up after 50 ms,
+    the host reads DJ_ETIMEOUT, and the next solve on the same context is exact."""
+    import torch
+    e = graphgen.bernoulli(5000, 0.01, 1, 100, seed=3)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    d = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    p = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    dj.dj_sssp_ex(G, 0, d, p, dj.make_solve_opts(engine=1, timeout_ns=50_000_000, debug_skip_cta=1))
+    with pytest.raises(dj.DjError) as ei:
+        dj.dj_sync()
+    assert ei.value.status == dj.DJ_ETIMEOUT
+    dj.dj_sync()  # the error word was cleared
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    assert_same(solve(dj, G, 0, engine=1), orc.dijkstra(W, 0), "after timeout")
+
+
+def test_host_result_entry_point(dj, orc):
+    e = graphgen.bernoulli(2500, 0.05, 1, 100, seed=8)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    d, p = dj.dj_sssp_host(G, 42)
+    assert_same((d, p), orc.dijkstra(W, 42), "host buffers")
+    # upload a modified matrix into the same graph and solve again
+    W2 = W.copy()
+    W2[42, :] = np.where(W2[42, :] == P.INF, P.INF, 1)
+    W2[42, 42] = 0
+    dj.dj_graph_upload(G, W2)
+    d, p = dj.dj_sssp_host(G, 42)
+    assert_same((d, p), orc.dijkstra(W2, 42), "after upload")
