@@ -1,0 +1,431 @@
+"""Benchmark: single-source dense Dijkstra solves per second at n=16384 on GB300.
+
+Workload (default): an undirected graph of n=16384 nodes, each pair an edge with
+probability 0.5, int32 weights uniform in [1, 1000] (a 1 GiB int32 adjacency
+matrix, larger than the 129 MB L2, so no flush is needed between steps), seed 2.
+One step = one complete solve (every phase of the hot path) from a seeded
+source; the sources cycle through 64 seeded distinct nodes.
+
+Printed (rank 0, one JSON line): SSSP/s of the device-resident solve (`value`),
+the same through the C ABI with host buffers and the matrix copied host->device
+every step (`e2e`, the paper's CUDA accounting: memory transfer + kernel), the
+roofline of the dominant kernel, the CPU oracle's SSSP/s on the host cores, the
+batched and plain-form throughputs, and the SM clocks sampled during the timed
+region.  ``--impl reference`` times the CPU oracle instead (bounded sample).
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own replica of
+the workload (independent solves, no collective on the data path) and the
+aggregate counts every rank's solves over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "dense_n16384_p0.5"
+BATCH_WORKLOAD = "multisource_n8192_p0.05_k256"
+INF = 2**31 - 1
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        t0 = self.marks[0] if self.marks else 0
+        t1 = self.marks[-1] if len(self.marks) > 1 else time.time()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, ln in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def _dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("DJ_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, rank, world, local
+    return None, 0, 1, 0
+
+
+def _barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def _max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    backend = dist.get_backend()
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if backend == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(per_rank_units: int, world: int, t_max_s: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return per_rank_units * world / t_max_s
+
+
+def cpu_oracle_rate(W: np.ndarray, sources, budget_s: float):
+    """Oracle solves per second on one host core, over a bounded sample (>= 1 solve)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.dijkstra(W, int(sources[done % len(sources)]))
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return done / el, done, el
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+    spec = graphgen.WORKLOADS[args.workload]
+    e = graphgen.make_graph(spec)
+    W = oracle.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+    srcs = graphgen.sources(e.n, 64, spec["seed"])
+    for i in range(min(args.warmup, 1)):
+        oracle.dijkstra(W, int(srcs[i % 64]))
+    # bounded: the K requested solves, or as many as fit in the time budget
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        oracle.dijkstra(W, int(srcs[done % 64]))
+        done += 1
+        if time.perf_counter() - t0 > args.reference_budget_s:
+            break
+    el = time.perf_counter() - t0
+    v = done / el
+    line = {"impl": "reference", "metric": "SSSP/s (single-source dense Dijkstra, n=16384)", "value": v,
+            "unit": "SSSP/s", "n_gpus": args.gpus, "steps": done, "steps_requested": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": e.n, "p": spec.get("p"), "weights": [spec["wlo"], spec["whi"]],
+                       "seed": spec["seed"], "l2": "inputs larger than L2 (1 GiB matrix)"},
+            "cpu_baseline": {"value": v, "unit": "SSSP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} serial Algorithm 1 solves (plain C, 1 thread) at n={e.n}"},
+            "e2e": {"value": v, "unit": "SSSP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    ap.add_argument("--reference-budget-s", type=float, default=90.0)
+    ap.add_argument("--soak-s", type=float, default=1.0, help="untimed load before warm-up (clock sampling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch / plain-form / e2e side measurements")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import graphgen
+    import __graft_entry__
+    dist, rank, world, local = _dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_2504_03667_gb300 import dj
+
+    spec = graphgen.WORKLOADS[args.workload]
+    e = graphgen.make_graph(spec)
+    n = e.n
+    g = dj.dj_load_edges(n, e.src, e.dst, e.w, e.directed)
+    srcs = graphgen.sources(n, 64, spec["seed"])
+    stream = torch.cuda.Stream()
+    dist_t = torch.empty(n, dtype=torch.int32, device="cuda")
+    pred_t = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def step(i):
+        dj.dj_sssp(g, int(srcs[i % 64]), dist_t, pred_t, stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    # untimed soak so the clock sampler sees the GPU under this load
+    t_soak = time.time()
+    i = 0
+    while time.time() - t_soak < args.soak_s:
+        step(i)
+        i += 1
+        if i % 50 == 0:
+            stream.synchronize()
+    for i in range(args.warmup):
+        step(i)
+    dj.dj_sync(stream)
+    _barrier(dist, local)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    e1.synchronize()
+    clocks.mark()
+    torch.cuda.synchronize()
+    _barrier(dist, local)
+    dj.dj_sync(stream)
+    clock_info = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    t_max = _max_over_ranks(dist, ms_total / 1e3)
+    value = aggregate(args.steps, world, t_max)
+    ms_per_step = 1e3 * t_max / args.steps
+    phases = dj.dj_last_phases()
+
+    # roofline of the dominant kernel (k_sssp_grid): algorithmic bytes = n^2 * 4 per solve
+    alg_bytes = n * n * 4
+    per_launch_s = (ms_total / 1e3) / args.steps
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = _peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "k_sssp_grid_dense_n16384_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                tj = json.load(f)
+            if tj.get("kernel_source_hash") == _kernel_hash():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+                "frac_of_8tbs": achieved / 8000.0, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": "k_sssp_grid"}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = side_measurements(dj, torch, graphgen, g, e, srcs, stream)
+
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        W = oracle.build_matrix(n, e.src, e.dst, e.w, e.directed)
+        rate, done, el = cpu_oracle_rate(W, srcs, args.cpu_budget_s)
+        cpu = {"value": rate, "unit": "SSSP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} serial Algorithm 1 solves (plain C, 1 thread) of the same n={n} workload in {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "SSSP/s (single-source dense Dijkstra, n=16384) and HBM GB/s vs 8 TB/s",
+            "value": value, "unit": "SSSP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "p": spec.get("p"), "weights": [spec["wlo"], spec["whi"]],
+                       "seed": spec["seed"], "sources": "64 seeded distinct, cycled", "engine": "grid (cooperative)",
+                       "mode": "phase-batched exact", "phases_last_solve": phases,
+                       "l2": "inputs larger than L2 (1 GiB matrix), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "hbm_gbs_algorithmic": achieved,
+            "cpu_baseline": cpu,
+            "clocks": clock_info,
+            "gpu_launches": args.steps,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dj_core.cuh", "dj_solve.cu", "dj_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2504_03667_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
+    """e2e through host buffers, the batched workload and the plain one-launch-per-solve form."""
+    out = {}
+    n = e.n
+    # e2e: matrix host->device (pinned) + solve + dist/pred device->host, every step
+    W_host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
+    Wnp = dj.dj_graph_download(g)
+    W_host.numpy()[:] = Wnp
+    del Wnp
+    dh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    ph = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    for i in range(2):
+        dj.dj_graph_upload(g, W_host, stream)
+        dj.dj_sssp_host(g, int(srcs[i]), dh, ph, stream)
+    steps = 10
+    t0 = time.perf_counter()
+    for i in range(steps):
+        dj.dj_graph_upload(g, W_host, stream)
+        dj.dj_sssp_host(g, int(srcs[i % 64]), dh, ph, stream)
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": steps / el, "unit": "SSSP/s", "h2d_bytes_per_step": n * n * 4,
+                  "d2h_bytes_per_step": 2 * n * 4, "steps": steps,
+                  "what": "dj_graph_upload (pinned host matrix) + dj_sssp_host (results to pinned host), per step"}
+    del W_host
+    # resident-graph e2e: only the source in and dist/pred out per step
+    t0 = time.perf_counter()
+    for i in range(50):
+        dj.dj_sssp_host(g, int(srcs[i % 64]), dh, ph, stream)
+    el = time.perf_counter() - t0
+    out["e2e_resident_graph"] = {"value": 50 / el, "unit": "SSSP/s", "h2d_bytes_per_step": 0,
+                                 "d2h_bytes_per_step": 2 * n * 4}
+    # plain form: literal Algorithm 1 (one node per step), one launch per solve, synchronous
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = torch.empty_like(d)
+    o = dj.make_solve_opts(mode=dj.DJ_MODE_PLAIN)
+    dj.dj_sssp_ex(g, int(srcs[0]), d, p, o, stream)
+    dj.dj_sync(stream)
+    t0 = time.perf_counter()
+    reps = 3
+    for i in range(reps):
+        dj.dj_sssp_ex(g, int(srcs[i]), d, p, o, stream)
+        dj.dj_sync(stream)
+    el = time.perf_counter() - t0
+    out["plain_form_n16384"] = {"value": reps / el, "unit": "SSSP/s",
+                                "what": "one node per step (Algorithm 1 literally), one launch per solve, synced"}
+    # batched workload: 256 sources of one n=8192 graph in one persistent launch
+    bspec = graphgen.WORKLOADS[BATCH_WORKLOAD]
+    be = graphgen.make_graph(bspec)
+    bg = dj.dj_load_edges(be.n, be.src, be.dst, be.w, be.directed)
+    bs = graphgen.sources(be.n, bspec["k"], bspec["seed"])
+    k = len(bs)
+    D = torch.empty((k, be.n), dtype=torch.int32, device="cuda")
+    P = torch.empty_like(D)
+    b = dj.dj_batch_create([bg] * k, bs, list(D), list(P))
+    tune = dj.dj_batch_autotune(b, stream)
+    for _ in range(2):
+        dj.dj_batch_launch(b, stream)
+    dj.dj_sync(stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        dj.dj_batch_launch(b, stream)
+    e1.record(stream)
+    e1.synchronize()
+    dj.dj_sync(stream)
+    batch_ms = e0.elapsed_time(e1) / reps
+    batch_rate = k / (batch_ms / 1e3)
+    # plain form on the batch graph: one plain launch per solve, synchronous
+    d2 = torch.empty(be.n, dtype=torch.int32, device="cuda")
+    p2 = torch.empty_like(d2)
+    o = dj.make_solve_opts(mode=dj.DJ_MODE_PLAIN)
+    dj.dj_sssp_ex(bg, int(bs[0]), d2, p2, o, stream)
+    dj.dj_sync(stream)
+    t0 = time.perf_counter()
+    reps2 = 5
+    for i in range(reps2):
+        dj.dj_sssp_ex(bg, int(bs[i]), d2, p2, o, stream)
+        dj.dj_sync(stream)
+    plain_rate = reps2 / (time.perf_counter() - t0)
+    # and the fast single-solve kernel, one launch per solve, synchronous
+    t0 = time.perf_counter()
+    for i in range(20):
+        dj.dj_sssp(bg, int(bs[i]), d2, p2, stream)
+        dj.dj_sync(stream)
+    single_rate = 20 / (time.perf_counter() - t0)
+    out["batch"] = {"workload": BATCH_WORKLOAD, "value": batch_rate, "unit": "SSSP/s", "ms_per_batch": batch_ms,
+                    "solves_per_batch": k, "autotune": tune,
+                    "hbm_gbs_algorithmic": k * be.n * be.n * 4 / (batch_ms / 1e3) / 1e9,
+                    "plain_form_value": plain_rate, "vs_plain_form": batch_rate / plain_rate,
+                    "phase_single_launch_value": single_rate, "vs_phase_single_launch": batch_rate / single_rate}
+    b.free()
+    bg.free()
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -202,6 +202,8 @@ WORKLOADS = {
     "sparse_directed_n32768_deg8": dict(kind="outdeg", n=32768, d=8, wlo=1, whi=10000, seed=3, source=None),
     "multisource_n8192_p0.05_k256": dict(kind="bernoulli", n=8192, p=0.05, wlo=1, whi=1000, seed=4, k=256),
     "serving_64graphs_10000req": dict(kind="serving", graphs=64, requests=10000, wlo=1, whi=1000, seed=5),
+    # a smaller dense case of the same shape for profiler captures (256 MiB matrix, still larger than L2)
+    "dense_n8192_p0.5": dict(kind="bernoulli", n=8192, p=0.5, wlo=1, whi=1000, seed=6, source=None),
 }
 
 

@@ -128,7 +128,11 @@ typedef struct dj_solve_opts {
   int32_t unroll;         /* rows in flight per warp (1, 2, 4 or 8), 0 = auto */
   int64_t timeout_ns;     /* limit of every in-kernel wait, 0 = 2 s */
   int32_t debug_skip_cta; /* testing only: this CTA leaves before the first grid barrier (-1 = none) */
-  int32_t reserved[5];
+  int32_t trace_cap;      /* grid engine profiling: entries of `trace` (0 = no trace) */
+  uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 records 4 words
+                             (%globaltimer at the phase's barrier exit, after staging, after the
+                             relaxation, and the settled-row count); unused entries are left as is */
+  int32_t reserved[2];
 } dj_solve_opts;
 
 /* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */

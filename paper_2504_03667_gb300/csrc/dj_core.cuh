@@ -104,7 +104,7 @@ __device__ __forceinline__ void block_min2(uint64_t& k, uint32_t& l, BlockScratc
 // Local partial of step 1: returns the slice's argmin key (dist << 32 | v) and
 // its settle bound L_c (already capped), and writes the candidates
 // {unvisited v : dist[v] < L_c} u {argmin} as (v, dist[v]) to `out`
-// (compacted, increasing v).  Returns the candidate count.  `plain` publishes
+// (compacted, in no particular order).  Returns the candidate count.  `plain` publishes
 // the argmin only.
 __device__ __forceinline__ int slice_publish(const Slice& s, uint32_t span, bool plain, uint2* out,
                                              uint64_t* key_out, uint32_t* Lc_out, BlockScratch* sc) {
@@ -132,9 +132,11 @@ __device__ __forceinline__ int slice_publish(const Slice& s, uint32_t span, bool
   *key_out = key;
   *Lc_out = Lc;
   if (mc >= kInf) return 0;
-  // compaction of {unvisited, dist < Lc} u {argmin}
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int base = 0;
+  // append {unvisited, dist < Lc} u {argmin}: one shared-memory atomic per warp
+  // (the order of the list is irrelevant: the relaxation keys are order-free)
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) sc->cnt[32] = 0;
+  __syncthreads();
   for (int j0 = 0; j0 < s.sw; j0 += blockDim.x) {
     const int j = j0 + threadIdx.x;
     bool p = false;
@@ -144,26 +146,17 @@ __device__ __forceinline__ int slice_publish(const Slice& s, uint32_t span, bool
       p = d < Lc || static_cast<uint32_t>(s.c0 + j) == ac;
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, p);
-    if (lane == 0) sc->cnt[w] = __popc(bal);
-    __syncthreads();
-    if (w == 0) {
-      uint32_t c = lane < nw ? sc->cnt[lane] : 0;
-      uint32_t incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane < nw) sc->cnt[lane] = incl - c;
-      if (lane == 31) sc->cnt[32] = incl;
+    if (bal) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (p) out[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(static_cast<uint32_t>(s.c0 + j), d);
     }
-    __syncthreads();
-    if (p) out[base + sc->cnt[w] + __popc(bal & ((1u << lane) - 1u))] =
-        make_uint2(static_cast<uint32_t>(s.c0 + j), d);
-    base += sc->cnt[32];
-    __syncthreads();
   }
-  return base;
+  __syncthreads();
+  const int total = static_cast<int>(sc->cnt[32]);
+  __syncthreads();
+  return total;
 }
 
 // Combine per-CTA partials (key, Lc) into the phase decision.
@@ -213,92 +206,169 @@ __device__ __forceinline__ Tile make_tile(int nvec, int rgs_cap) {
   return t;
 }
 
-template <int V>
-__device__ __forceinline__ void best_reset(uint64_t (&best)[V][4]) {
+// Settled rows are staged in shared memory as their 32-bit tie-break word
+// tb = ((dist[u] - m) << bits_u) | u  (dist[u] = m + (tb >> bits_u)).
+// stage_list appends the settled entries among candidates [begin, end) of
+// `get` to `list` (order irrelevant) and returns the new count.  Ends synced.
+template <class Get>
+__device__ __forceinline__ int stage_list(const Get& get, int begin, int end, const Decision& D, uint32_t bits_u,
+                                          uint32_t* list, int base, BlockScratch* sc) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) sc->cnt[32] = static_cast<uint32_t>(base);
+  __syncthreads();
+  constexpr int K = 4;
+  for (int i0 = begin; i0 < end; i0 += K * blockDim.x) {
+    uint2 e[K];
 #pragma unroll
-  for (int k = 0; k < V; ++k)
+    for (int k = 0; k < K; ++k) {
+      const int i = i0 + k * blockDim.x + threadIdx.x;
+      e[k] = i < end ? get(i) : make_uint2(0xffffffffu, kInf);
+    }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) best[k][c] = kNoKey;
-}
-
-// Apply U rows (entries e[], already filtered: e.x == 0xffffffff marks an
-// empty slot) to the lane's columns.
-template <int V, int U>
-__device__ __forceinline__ void relax_rows(const uint2 (&e)[U], const int32_t* __restrict__ Wc0, int64_t pitch,
-                                           const int (&jv)[V], const bool (&jok)[V], uint32_t m,
-                                           uint32_t bits_u, uint64_t (&best)[V][4]) {
-  int4 x[U][V];
-#pragma unroll
-  for (int uu = 0; uu < U; ++uu) {
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      if (e[uu].x != 0xffffffffu && jok[k]) {
-        x[uu][k] = ld_stream16(Wc0 + static_cast<int64_t>(e[uu].x) * pitch + 4 * jv[k]);
-      } else {
-        x[uu][k] = make_int4(int(kInf), int(kInf), int(kInf), int(kInf));
+    for (int k = 0; k < K; ++k) {
+      const bool p = e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, D);
+      const uint32_t bal = __ballot_sync(0xffffffffu, p);
+      if (bal) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (p) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((e[k].y - D.m) << bits_u) | e[k].x;
       }
     }
   }
+  __syncthreads();
+  const int total = static_cast<int>(sc->cnt[32]);
+  __syncthreads();
+  return total;
+}
+
+// A warp's ring of `depth` stages x U row slots in shared memory, filled by
+// 1-D TMA bulk copies (one per row) that complete on the stage's mbarrier.
+// Only this warp issues into and reads from its ring, so no other warp ever
+// waits on it.  `gt` counts the warp's stages over the whole kernel: stage g
+// uses slot g % depth and waits for parity (g / depth) & 1 (depth = 2^lg).
+struct Ring {
+  uint8_t* buf;
+  uint64_t* bar;
+  uint32_t lg;        // log2(depth)
+  uint32_t rowbytes;  // bytes of this warp's column chunk of one row (0: idle warp)
+  uint32_t gt;
+};
+
+// Per-column running best of one relaxation pass: candidate value bc and its
+// tie-break word bt.  It starts at (dist[v], 0): a candidate that does not beat
+// the current dist can never be committed, and a tie with it never wins.
+template <int V>
+struct Best {
+  uint32_t bc[V][4];
+  uint32_t bt[V][4];
+};
+
+template <int V>
+__device__ __forceinline__ void best_init(Best<V>& b, const Slice& s, const Tile& t) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int uu = 0; uu < U; ++uu) {
-    const uint32_t du = e[uu].x != 0xffffffffu ? e[uu].y : kInf;
-    const uint32_t tb = ((du - m) << bits_u) | (e[uu].x & ((1u << bits_u) - 1u));
+  for (int k = 0; k < V; ++k) {
+    const int jv = (t.wc * V + k) * 32 + lane;
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-      const uint32_t c0 = du + static_cast<uint32_t>(x[uu][k].x);
-      const uint32_t c1 = du + static_cast<uint32_t>(x[uu][k].y);
-      const uint32_t c2 = du + static_cast<uint32_t>(x[uu][k].z);
-      const uint32_t c3 = du + static_cast<uint32_t>(x[uu][k].w);
-      const uint64_t k0 = (static_cast<uint64_t>(c0) << 32) | tb;
-      const uint64_t k1 = (static_cast<uint64_t>(c1) << 32) | tb;
-      const uint64_t k2 = (static_cast<uint64_t>(c2) << 32) | tb;
-      const uint64_t k3 = (static_cast<uint64_t>(c3) << 32) | tb;
-      best[k][0] = k0 < best[k][0] ? k0 : best[k][0];
-      best[k][1] = k1 < best[k][1] ? k1 : best[k][1];
-      best[k][2] = k2 < best[k][2] ? k2 : best[k][2];
-      best[k][3] = k3 < best[k][3] ? k3 : best[k][3];
+    for (int c = 0; c < 4; ++c) {
+      b.bc[k][c] = (t.active && jv < s.nvec) ? s.dist[4 * jv + c] : kInf;
+      b.bt[k][c] = 0;
     }
   }
 }
 
-// Relaxation over `cnt` entries produced by `get(i)` (entries are (u, dist[u])
-// candidates; the ones outside the settled set are skipped).  Entries of the
-// next iteration are fetched before the current rows are consumed.
-template <int V, int U, class Get>
-__device__ __forceinline__ void relax_entries(const Get& get, int cnt, const Slice& s, const Tile& t,
-                                              const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
-                                              uint32_t bits_u, uint64_t (&best)[V][4]) {
-  if (!t.active) return;
+__device__ __forceinline__ void best_update(uint32_t c, uint32_t tb, uint32_t& bc, uint32_t& bt) {
+  if (c < bc || (c == bc && tb < bt)) {
+    bc = c;
+    bt = tb;
+  }
+}
+
+// Relax the `cnt` staged rows over this CTA's slice.  Row group rg takes
+// list entries rg, rg + rgs, ...; its column-chunk warp streams those rows'
+// slices through its ring `depth` stages ahead of the arithmetic.  The common
+// case (no lane improves or ties its column) costs four adds, four compares
+// and one vote per row; the exact lexicographic update runs only otherwise.
+template <int V, int U>
+__device__ __forceinline__ bool relax_list(const uint32_t* __restrict__ list, int cnt, const Slice& s, const Tile& t,
+                                           const int32_t* __restrict__ W, int64_t pitch, uint32_t m, uint32_t bits_u,
+                                           Ring& ring, int64_t timeout_ns, Best<V>& best) {
+  if (!t.active || ring.rowbytes == 0) return true;
   const int lane = threadIdx.x & 31;
-  int jv[V];
   bool jok[V];
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    jv[k] = (t.wc * V + k) * 32 + lane;
-    jok[k] = jv[k] < s.nvec;
-  }
-  const int32_t* Wc0 = W + s.c0;
-  const int step = t.rgs * U;
-  uint2 nxt[U];
-#pragma unroll
-  for (int uu = 0; uu < U; ++uu) {
-    const int idx = t.rg + uu * t.rgs;
-    nxt[uu] = idx < cnt ? get(idx) : make_uint2(0xffffffffu, kInf);
-  }
-  for (int i = t.rg; i < cnt; i += step) {
-    uint2 e[U];
+  for (int k = 0; k < V; ++k) jok[k] = (t.wc * V + k) * 32 + lane < s.nvec;
+  const uint32_t umask = (1u << bits_u) - 1u;
+  const uint32_t dmask = (1u << ring.lg) - 1u;
+  const int J = t.rg < cnt ? (cnt - t.rg + t.rgs - 1) / t.rgs : 0;
+  const int nst = (J + U - 1) / U;
+  const char* colbase = reinterpret_cast<const char*>(W + s.c0) + static_cast<size_t>(t.wc) * V * 32 * 16;
+  const int64_t rowstride = pitch * 4;
+  const uint32_t* mylist = list + t.rg;
+  const int rgs = t.rgs;
+  auto issue = [&](int st) {
+    const uint32_t slot = (ring.gt + static_cast<uint32_t>(st)) & dmask;
+    const int rows = min(U, J - st * U);
+    uint64_t* bar = ring.bar + slot;
+    if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(rows) * ring.rowbytes);
+    __syncwarp();
+    if (lane < rows) {
+      const uint32_t u = mylist[(st * U + lane) * rgs] & umask;
+      bulk_g2s(ring.buf + (static_cast<size_t>(slot) * U + lane) * ring.rowbytes,
+               colbase + static_cast<int64_t>(u) * rowstride, ring.rowbytes, bar);
+    }
+  };
+  const int depth = 1 << ring.lg;
+  const int pre = min(depth, nst);
+  for (int st = 0; st < pre; ++st) issue(st);
+  bool ok = true;
+  for (int st = 0; st < nst; ++st) {
+    const uint32_t g = ring.gt + static_cast<uint32_t>(st);
+    const uint32_t slot = g & dmask;
+    const uint32_t parity = (g >> ring.lg) & 1u;
+    if (!mbar_wait_bounded(ring.bar + slot, parity, timeout_ns)) {
+      ok = false;
+      mbar_wait_bounded(ring.bar + slot, parity, timeout_ns);  // drain once more
+    }
+    const int rows = min(U, J - st * U);
+    const uint8_t* sb = ring.buf + static_cast<size_t>(slot) * U * ring.rowbytes + 16 * lane;
+    const uint32_t* lrow = mylist + st * U * rgs;
 #pragma unroll
     for (int uu = 0; uu < U; ++uu) {
-      e[uu] = nxt[uu];
-      if (e[uu].x != 0xffffffffu && !in_settled(e[uu].x, e[uu].y, D)) e[uu].x = 0xffffffffu;
-    }
+      if (uu < rows) {
+        const uint32_t tb = lrow[uu * rgs];
+        const uint32_t du = m + (tb >> bits_u);
+        uint32_t c[V][4];
+        bool hit = false;
 #pragma unroll
-    for (int uu = 0; uu < U; ++uu) {
-      const int idx = i + step + uu * t.rgs;
-      nxt[uu] = idx < cnt ? get(idx) : make_uint2(0xffffffffu, kInf);
+        for (int k = 0; k < V; ++k) {
+          if (jok[k]) {
+            const int4 x = *reinterpret_cast<const int4*>(sb + static_cast<size_t>(uu) * ring.rowbytes + 512 * k);
+            c[k][0] = du + static_cast<uint32_t>(x.x);
+            c[k][1] = du + static_cast<uint32_t>(x.y);
+            c[k][2] = du + static_cast<uint32_t>(x.z);
+            c[k][3] = du + static_cast<uint32_t>(x.w);
+            hit |= (c[k][0] <= best.bc[k][0]) | (c[k][1] <= best.bc[k][1]) | (c[k][2] <= best.bc[k][2]) |
+                   (c[k][3] <= best.bc[k][3]);
+          } else {
+            c[k][0] = c[k][1] = c[k][2] = c[k][3] = 0xFFFFFFFFu;
+          }
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+          for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) best_update(c[k][q], tb, best.bc[k][q], best.bt[k][q]);
+        }
+      }
     }
-    relax_rows<V, U>(e, Wc0, pitch, jv, jok, D.m, bits_u, best);
+    __syncwarp();
+    fence_proxy_async_smem();  // this slot's reads are done before its next TMA write
+    if (st + depth < nst) issue(st + depth);
   }
+  ring.gt += static_cast<uint32_t>(nst);
+  return ok;
 }
 
 __device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key, uint32_t bits_u) {
@@ -309,10 +379,10 @@ __device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key
   }
 }
 
-// Merge the row groups' keys and commit.  Ends synced.
+// Merge the row groups' bests and commit.  Ends synced.
 template <int V>
 __device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint64_t* merge, uint32_t bits_u,
-                                             uint64_t (&best)[V][4]) {
+                                             const Best<V>& best) {
   const int lane = threadIdx.x & 31;
   if (t.rgs == 1) {
     if (t.active) {
@@ -321,7 +391,8 @@ __device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint
         const int jv = (t.wc * V + k) * 32 + lane;
         if (jv < s.nvec) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) commit_key(s, 4 * jv + c, best[k][c], bits_u);
+          for (int c = 0; c < 4; ++c)
+            commit_key(s, 4 * jv + c, (static_cast<uint64_t>(best.bc[k][c]) << 32) | best.bt[k][c], bits_u);
         }
       }
     }
@@ -335,7 +406,7 @@ __device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint
       if (jv < s.nvec) {
         uint64_t* dst = merge + static_cast<size_t>(t.rg) * s.sw + 4 * jv;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) dst[c] = best[k][c];
+        for (int c = 0; c < 4; ++c) dst[c] = (static_cast<uint64_t>(best.bc[k][c]) << 32) | best.bt[k][c];
       }
     }
   }

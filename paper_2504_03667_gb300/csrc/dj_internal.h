@@ -86,6 +86,10 @@ struct ClusterPlan {
   size_t smem = 0;
   int swcap = 0;
   int rgs_cap = 0;
+  int list_cap = 0;
+  int depth = 0;
+  int rowcap = 0;
+  uint32_t* words = nullptr;
 };
 int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan);
 int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st);

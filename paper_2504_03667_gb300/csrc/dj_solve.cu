@@ -49,6 +49,11 @@ struct GridParams {
   int32_t swcap;
   int32_t rgs_cap;
   int32_t skip_cta;
+  int32_t list_cap;  // staged settled rows per segment
+  int32_t depth;     // ring stages per warp
+  int32_t rowcap;    // bytes of one ring row slot
+  int32_t trace_cap;
+  uint64_t* trace;   // optional per-phase timeline (CTA 0)
 };
 
 // Grid-wide barrier on a monotonic arrival counter (zeroed before launch).
@@ -80,6 +85,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uin
       }
     }
     __threadfence();
+    if (ok && ld_relaxed_gpu(abort_flag)) ok = 0;
     *s_flag = ok;
   }
   __syncthreads();
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   s.sw = 4 * s.nvec;
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
-  q += static_cast<size_t>(p.rgs_cap) * p.swcap * 8;
+  q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
   uint2* own = reinterpret_cast<uint2*>(q);
   q += static_cast<size_t>(p.swcap) * 8;
   s.dist = reinterpret_cast<uint32_t*>(q);
@@ -113,9 +119,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   s.minout = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
+  q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+  uint32_t* list = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.list_cap) * 4;
+  q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* rings = q;
+  q += static_cast<size_t>(blockDim.x >> 5) * p.depth * U * p.rowcap;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(q);
 
   slice_init(s, p.n, p.source, p.minout, !p.plain);
   const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
+  Ring ring;
+  ring.buf = rings + static_cast<size_t>(warp) * p.depth * U * p.rowcap;
+  ring.bar = bars + static_cast<size_t>(warp) * p.depth;
+  ring.lg = static_cast<uint32_t>(__ffs(p.depth) - 1);
+  ring.gt = 0;
+  ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
+  if (lane == 0)
+    for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
+  fence_mbar_init();
   __syncthreads();
 
   uint32_t* bar = p.ctl;
@@ -163,18 +186,39 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     __syncthreads();
     const Decision D = s_dec;
     const int total = static_cast<int>(s_word);
+    const bool tr = p.trace && b == 0 && threadIdx.x == 0 && static_cast<int>(4 * phase + 3) < p.trace_cap;
+    if (tr) p.trace[4 * phase] = global_ns();
     if (D.m >= kInf) break;
     slice_mark(s, D);
-    // 4. fused relaxation of the settled rows over this slice
-    uint64_t best[V][4];
-    best_reset<V>(best);
+    int staged = 0;
+    uint64_t t_staged = 0;
+    // 4. stage the settled rows, then stream their slices through the warps' rings
+    Best<V> best;
+    best_init<V>(best, s, t);
+    bool ok = true;
     if (p.plain) {
-      const uint2 one = make_uint2(D.a, D.m);
-      relax_entries<V, U>([one](int) { return one; }, 1, s, t, p.W, p.pitch, D, p.bits_u, best);
+      if (threadIdx.x == 0) list[0] = D.a;  // its tie-break word: (m - m) << bits | a
+      __syncthreads();
+      ok = relax_list<V, U>(list, 1, s, t, p.W, p.pitch, D.m, p.bits_u, ring, p.timeout_ns, best);
     } else {
-      const uint2* list = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap;
-      relax_entries<V, U>([list](int i) { return __ldcg(list + i); }, total, s, t, p.W, p.pitch, D, p.bits_u,
-                          best);
+      const uint2* cl = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap;
+      for (int seg = 0; seg < total; seg += p.list_cap) {
+        const int cnt = stage_list([cl](int i) { return __ldcg(cl + i); }, seg, min(total, seg + p.list_cap), D,
+                                   p.bits_u, list, 0, &sc);
+        staged += cnt;
+        if (tr && seg == 0) t_staged = global_ns();
+        ok = relax_list<V, U>(list, cnt, s, t, p.W, p.pitch, D.m, p.bits_u, ring, p.timeout_ns, best) && ok;
+        __syncthreads();  // the list is rewritten by the next segment
+      }
+    }
+    if (!ok) {
+      atomicOr(p.words, kErrTimeout);
+      atomicExch(abort_flag, 1u);
+    }
+    if (tr) {
+      p.trace[4 * phase + 1] = t_staged;
+      p.trace[4 * phase + 2] = global_ns();
+      p.trace[4 * phase + 3] = static_cast<uint64_t>(p.plain ? 1 : staged);
     }
     merge_commit<V>(s, t, merge, p.bits_u, best);
     ++phase;
@@ -188,13 +232,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
 struct ClusterParams {
   const SolveDesc* descs;
   uint32_t* queue;  // [0] next solve index (zeroed before launch)
+  uint32_t* words;  // per-device words: [0] error bits
+  int64_t timeout_ns;
   int32_t k;
   int32_t swcap;
   int32_t rgs_cap;
+  int32_t list_cap;
+  int32_t depth;
+  int32_t rowcap;
 };
 
 template <int V, int U, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p) {
+__global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BlockScratch sc;
   __shared__ __align__(16) uint4 s_part[2];  // this CTA's published partial, per phase parity
@@ -207,7 +256,7 @@ __global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p)
   const uint32_t rank = cluster_rank(), C = cluster_size();
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
-  q += static_cast<size_t>(p.rgs_cap) * p.swcap * 8;
+  q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
   uint2* own = reinterpret_cast<uint2*>(q);  // [2][swcap]
   q += static_cast<size_t>(p.swcap) * 16;
   Slice s;
@@ -218,6 +267,23 @@ __global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p)
   s.minout = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
+  q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+  uint32_t* list = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.list_cap) * 4;
+  q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* rings = q;
+  q += static_cast<size_t>(blockDim.x >> 5) * p.depth * U * p.rowcap;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(q);
+  Ring ring;
+  ring.buf = rings + static_cast<size_t>(warp) * p.depth * U * p.rowcap;
+  ring.bar = bars + static_cast<size_t>(warp) * p.depth;
+  ring.lg = static_cast<uint32_t>(__ffs(p.depth) - 1);
+  ring.gt = 0;
+  if (lane == 0)
+    for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
+  fence_mbar_init();
+  __syncthreads();
 
   for (;;) {
     // next solve: rank 0 takes it from the queue, every CTA reads it through DSMEM
@@ -239,6 +305,7 @@ __global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p)
     s.sw = 4 * s.nvec;
     slice_init(s, d.n, d.source, d.minout, !d.plain);
     const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
+    ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
     __syncthreads();
 
     uint32_t phase = 0;
@@ -279,19 +346,24 @@ __global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p)
       const Decision D = s_dec;
       if (D.m >= kInf) break;
       slice_mark(s, D);
-      uint64_t best[V][4];
-      best_reset<V>(best);
+      Best<V> best;
+      best_init<V>(best, s, t);
       const int total = static_cast<int>(s_off[C]);
       const int Cn = static_cast<int>(C);
-      relax_entries<V, U>(
-          [Cn](int i) {
-            int r = 0;
+      auto get = [Cn](int i) {
+        int r = 0;
 #pragma unroll
-            for (int st = 8; st >= 1; st >>= 1)
-              if (r + st < Cn && static_cast<int>(s_off[r + st]) <= i) r += st;
-            return ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
-          },
-          total, s, t, d.W, d.pitch, D, d.bits_u, best);
+        for (int st = 8; st >= 1; st >>= 1)
+          if (r + st < Cn && static_cast<int>(s_off[r + st]) <= i) r += st;
+        return ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
+      };
+      bool ok = true;
+      for (int seg = 0; seg < total; seg += p.list_cap) {
+        const int cnt = stage_list(get, seg, min(total, seg + p.list_cap), D, d.bits_u, list, 0, &sc);
+        ok = relax_list<V, U>(list, cnt, s, t, d.W, d.pitch, D.m, d.bits_u, ring, p.timeout_ns, best) && ok;
+        __syncthreads();
+      }
+      if (!ok) atomicOr(p.words, kErrTimeout);
       merge_commit<V>(s, t, merge, d.bits_u, best);
       ++phase;
     }
@@ -303,19 +375,31 @@ __global__ void __launch_bounds__(THREADS) k_sssp_cluster(const ClusterParams p)
 
 namespace {
 
-template <int V>
-struct UFor {
-  static constexpr int value = V == 1 ? 8 : (V == 2 ? 4 : 2);
-};
-
+constexpr int kRowsPerStage = 8;  // U: rows per ring stage
 constexpr int kGridThreads = 512;
 constexpr int kClusterThreads = 256;
 
-size_t grid_smem(int swcap, int rgs_cap) {
-  return static_cast<size_t>(rgs_cap) * swcap * 8 + static_cast<size_t>(swcap) * (8 + 12 + 1) + 16;
-}
-size_t cluster_smem(int swcap, int rgs_cap) {
-  return static_cast<size_t>(rgs_cap) * swcap * 8 + static_cast<size_t>(swcap) * (16 + 12 + 1) + 16;
+// Shared-memory layout of one CTA (must match the carving in the kernels).
+struct Layout {
+  int V = 0;
+  int swcap = 0;    // columns of the widest slice
+  int rgs_cap = 0;  // row groups (merge buffer rows)
+  int list_cap = 0; // staged settled rows per segment
+  int depth = 0;    // ring stages per warp
+  int rowcap = 0;   // bytes of one ring row slot
+  size_t smem = 0;
+};
+
+size_t layout_bytes(const Layout& L, int nwarps, int own_copies) {
+  size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (unused with one row group)
+  b += static_cast<size_t>(L.swcap) * 8 * own_copies;        // published candidates
+  b += static_cast<size_t>(L.swcap) * 12;                     // dist, pred, minout
+  b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;         // visited
+  b += static_cast<size_t>(L.list_cap) * 4;                   // staged rows
+  b += 128;                                                   // ring alignment
+  b += static_cast<size_t>(nwarps) * L.depth * kRowsPerStage * L.rowcap;
+  b += static_cast<size_t>(nwarps) * L.depth * 8;             // mbarriers
+  return b;
 }
 
 // smallest V in {1, 2, 4} whose column chunks fit the warps (at least one row group)
@@ -325,13 +409,35 @@ int pick_v(int nvec_cta, int nwarps) {
   return 0;
 }
 
+// Fit the layout into `budget` bytes: ring depth first (down to 1), then the list.
+int make_layout(int nvec_cta, int nwarps, int own_copies, int want_depth, int want_list, size_t budget, Layout* L) {
+  L->V = pick_v(nvec_cta, nwarps);
+  if (!L->V) return set_error(DJ_EUNSUPPORTED, "graph too large for this engine configuration");
+  L->swcap = 4 * std::max(nvec_cta, 1);
+  const int wpr = std::max(1, (nvec_cta + 32 * L->V - 1) / (32 * L->V));
+  L->rgs_cap = std::max(1, nwarps / wpr);
+  L->rowcap = std::min(32 * L->V, std::max(nvec_cta, 1)) * 16;
+  want_list = std::max(want_list, 32);
+  for (int depth = want_depth; depth >= 1; depth /= 2) {
+    // keep segments long (>= 512 rows) while ring depth can still give way
+    const int min_list = depth > 1 ? std::min(512, want_list) : 32;
+    for (int list = want_list; list >= min_list; list /= 2) {
+      L->depth = depth;
+      L->list_cap = list;
+      L->smem = layout_bytes(*L, nwarps, own_copies);
+      if (L->smem <= budget) return DJ_OK;
+    }
+  }
+  return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
+}
+
 template <int V>
 void* grid_kernel() {
-  return reinterpret_cast<void*>(&k_sssp_grid<V, UFor<V>::value, kGridThreads>);
+  return reinterpret_cast<void*>(&k_sssp_grid<V, kRowsPerStage, kGridThreads>);
 }
 template <int V>
 void* cluster_kernel() {
-  return reinterpret_cast<void*>(&k_sssp_cluster<V, UFor<V>::value, kClusterThreads>);
+  return reinterpret_cast<void*>(&k_sssp_cluster<V, kRowsPerStage, kClusterThreads>);
 }
 void* grid_kernel_for(int v) {
   switch (v) {
@@ -350,6 +456,12 @@ void* cluster_kernel_for(int v) {
   return nullptr;
 }
 
+int round_pow2_down(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
 }  // namespace
 
 int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
@@ -361,23 +473,19 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   const int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
   int G = std::min(ctx->num_sms * per_sm, nvec_total);
   const int nwarps = kGridThreads / 32;
-  int nvec_cta = (nvec_total + G - 1) / G;
-  const int V = pick_v(nvec_cta, nwarps);
-  if (!V) return set_error(DJ_EUNSUPPORTED, "graph too large for the grid engine");
-  const int swcap = 4 * nvec_cta;
-  const int wpr = (nvec_cta + 32 * V - 1) / (32 * V);
-  int rgs_cap = nwarps / wpr;
-  while (rgs_cap > 1 && grid_smem(swcap, rgs_cap) > static_cast<size_t>(ctx->max_smem_optin) - 4096) --rgs_cap;
-  const size_t smem = grid_smem(swcap, rgs_cap);
-  if (smem > static_cast<size_t>(ctx->max_smem_optin)) return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
-  void* fn = grid_kernel_for(V);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const int nvec_cta = (nvec_total + G - 1) / G;
+  const int want_depth = o.unroll > 0 ? round_pow2_down(std::min(o.unroll, 16)) : 2;
+  const size_t budget = static_cast<size_t>(ctx->max_smem_optin) / per_sm - 1024;
+  Layout L;
+  if (int rc = make_layout(nvec_cta, nwarps, 1, want_depth, g->pitch, budget, &L)) return rc;
+  void* fn = grid_kernel_for(L.V);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, L.smem);
   if (e != cudaSuccess) return cuda_error(e, "occupancy query");
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "grid engine cannot be resident");
-  if (occ < per_sm) G = std::min(ctx->num_sms * occ, nvec_total);
+  if (occ < per_sm) return set_error(DJ_EUNSUPPORTED, "requested CTAs per SM cannot be resident");
 
   const size_t ctl_bytes = 256;
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
@@ -406,33 +514,34 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
   p.span = host_span_for(static_cast<uint32_t>(g->n));
   p.cand_cap = cand_cap;
-  p.swcap = swcap;
-  p.rgs_cap = rgs_cap;
+  p.swcap = L.swcap;
+  p.rgs_cap = L.rgs_cap;
   p.skip_cta = o.debug_skip_cta;
+  p.list_cap = L.list_cap;
+  p.depth = L.depth;
+  p.rowcap = L.rowcap;
+  p.trace_cap = o.trace ? o.trace_cap : 0;
+  p.trace = o.trace;
   void* args[] = {&p};
-  e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, smem, st);
+  e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
   return DJ_OK;
 }
 
-static int cluster_dims(int32_t max_pitch, const ClusterLaunch& cl, int* V, int* swcap, int* rgs_cap, size_t* smem) {
+static int cluster_layout(int32_t max_pitch, const ClusterLaunch& cl, Layout* L) {
   DevCtx* ctx = nullptr;
   if (int rc = get_ctx(&ctx)) return rc;
   const int C = cl.cluster_size;
   const int nvec_total = max_pitch / 4;
   const int nvec_cta = (nvec_total + C - 1) / C;
   const int nwarps = kClusterThreads / 32;
-  *V = pick_v(nvec_cta, nwarps);
-  if (!*V) return set_error(DJ_EUNSUPPORTED, "graph too large for this cluster size");
-  *swcap = 4 * std::max(nvec_cta, 1);
-  const int wpr = (nvec_cta + 32 * *V - 1) / (32 * *V);
-  *rgs_cap = std::max(1, nwarps / std::max(wpr, 1));
-  while (*rgs_cap > 1 && cluster_smem(*swcap, *rgs_cap) > static_cast<size_t>(ctx->max_smem_optin) - 4096) --*rgs_cap;
-  *smem = cluster_smem(*swcap, *rgs_cap);
-  if (*smem > static_cast<size_t>(ctx->max_smem_optin))
-    return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory for this cluster size");
-  return DJ_OK;
+  // two CTAs per SM when they fit, so clusters of different solves share SMs
+  const size_t half = static_cast<size_t>(ctx->max_smem_optin) / 2 - 1024;
+  const int want_list = std::min(max_pitch, 8192);
+  if (make_layout(nvec_cta, nwarps, 2, 2, want_list, half, L) == DJ_OK) return DJ_OK;
+  clear_error();
+  return make_layout(nvec_cta, nwarps, 2, 2, want_list, static_cast<size_t>(ctx->max_smem_optin) - 1024, L);
 }
 
 static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
@@ -446,17 +555,16 @@ static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
 }
 
 int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters) {
-  int V, swcap, rgs_cap;
-  size_t smem;
-  if (int rc = cluster_dims(max_pitch, cl, &V, &swcap, &rgs_cap, &smem)) return rc;
-  void* fn = cluster_kernel_for(V);
-  if (int rc = prepare_cluster(fn, cl, smem)) return rc;
+  Layout L;
+  if (int rc = cluster_layout(max_pitch, cl, &L)) return rc;
+  void* fn = cluster_kernel_for(L.V);
+  if (int rc = prepare_cluster(fn, cl, L.smem)) return rc;
   cudaLaunchConfig_t cfg = {};
   DevCtx* ctx = nullptr;
   get_ctx(&ctx);
   cfg.gridDim = dim3(cl.cluster_size * ctx->num_sms);
   cfg.blockDim = dim3(kClusterThreads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = L.smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cl.cluster_size;
@@ -481,22 +589,27 @@ bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl) {
 
 int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan) {
   if (cl.cluster_size < 1 || cl.cluster_size > 16) return set_error(DJ_EINVAL, "cluster size must be 1..16");
-  int V, swcap, rgs_cap;
-  size_t smem;
-  if (int rc = cluster_dims(max_pitch, cl, &V, &swcap, &rgs_cap, &smem)) return rc;
-  void* fn = cluster_kernel_for(V);
-  if (int rc = prepare_cluster(fn, cl, smem)) return rc;
+  Layout L;
+  if (int rc = cluster_layout(max_pitch, cl, &L)) return rc;
+  void* fn = cluster_kernel_for(L.V);
+  if (int rc = prepare_cluster(fn, cl, L.smem)) return rc;
   int Q = cl.clusters;
   if (Q <= 0) {
     if (int rc = cluster_max_clusters(max_pitch, cl, &Q)) return rc;
   }
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
   plan->fn = fn;
   plan->clusters = std::max(1, std::min(Q, std::max(k, 1)));
   plan->cluster_size = cl.cluster_size;
   plan->threads = kClusterThreads;
-  plan->smem = smem;
-  plan->swcap = swcap;
-  plan->rgs_cap = rgs_cap;
+  plan->smem = L.smem;
+  plan->swcap = L.swcap;
+  plan->rgs_cap = L.rgs_cap;
+  plan->list_cap = L.list_cap;
+  plan->depth = L.depth;
+  plan->rowcap = L.rowcap;
+  plan->words = ctx->words;
   return DJ_OK;
 }
 
@@ -506,9 +619,14 @@ int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, 
   ClusterParams p;
   p.descs = descs_dev;
   p.queue = queue;
+  p.words = plan.words;
+  p.timeout_ns = 2000000000LL;
   p.k = k;
   p.swcap = plan.swcap;
   p.rgs_cap = plan.rgs_cap;
+  p.list_cap = plan.list_cap;
+  p.depth = plan.depth;
+  p.rowcap = plan.rowcap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(plan.clusters * plan.cluster_size));
   cfg.blockDim = dim3(static_cast<unsigned>(plan.threads));

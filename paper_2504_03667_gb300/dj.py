@@ -50,7 +50,7 @@ class dj_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("engine", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("debug_skip_cta", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("trace_cap", ctypes.c_int32), ("trace", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
 
 
 class dj_batch_opts(ctypes.Structure):
@@ -268,11 +268,14 @@ def dj_graph_free(g):
 # ---------------------------------------------------------------------- solves
 
 def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, threads=0, ctas_per_sm=0,
-                    unroll=0, timeout_ns=0, debug_skip_cta=-1) -> dj_solve_opts:
+                    unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None) -> dj_solve_opts:
+    """trace: optional int64 CUDA tensor receiving the grid engine's per-phase timeline."""
     o = dj_solve_opts()
     load_library().dj_solve_opts_init(ctypes.byref(o))
     o.mode, o.engine, o.cluster_size, o.threads = mode, engine, cluster_size, threads
     o.ctas_per_sm, o.unroll, o.timeout_ns, o.debug_skip_cta = ctas_per_sm, unroll, timeout_ns, debug_skip_cta
+    if trace is not None:
+        o.trace, o.trace_cap = int(trace.data_ptr()), int(trace.numel())
     return o
 
 
