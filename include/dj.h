@@ -161,6 +161,32 @@ int dj_sync(uint64_t stream);
  * by dj_sssp/dj_sssp_ex on this device; -1 if unknown.  Call after dj_sync. */
 int dj_last_phases(void);
 
+/* Allocation-free single solve.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory at solve
+ * time -- for example code running while a stream is being captured under a
+ * global capture mode (where cudaMalloc is forbidden), serving loops that
+ * cannot afford the device-wide synchronisation or the failure of a late
+ * allocation, or processes whose caching allocator already reserved nearly
+ * all of HBM.  It runs the same grid-engine kernel and gives the same dist
+ * and pred as dj_sssp, but its scratch (barrier and candidate counters,
+ * per-CTA partials and the two candidate lists, 2 * 8 * pitch bytes) lives in
+ * one fixed 4 MiB array compiled into the library: every GPU that loads the
+ * library holds those 4 MiB until the process exits.  Graphs whose scratch
+ * does not fit (n above about 261,000) are rejected with DJ_EINVAL.
+ *   g, source, dist, pred, stream: as dj_sssp (dist/pred DEVICE pointers).
+ * The call allocates no device memory: it issues two small cudaMemsetAsync
+ * calls (clearing the counters and setting dist[source] = -1) and one kernel
+ * launch on `stream`.  Asynchronous: once the stream has passed the kernel,
+ * dist[source] == 0 means the solve completed; dist[source] == -1 means a
+ * bounded in-kernel wait ran out and the outputs are not valid.
+ * The first call on each device performs a one-time set-up (it looks up the
+ * array's device address and the device's attributes); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * it keeps the previous call's contents, so calls whose kernels overlap on the
+ * GPU (for instance on two streams) race: order them on one stream or
+ * synchronise between them. */
+int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
+
 /* ------------------------------------------------------------------ batched solves */
 /* k solves (graph[i], sources[i]) in ONE persistent launch: one thread-block
  * cluster per solve at a time, solves pulled from a device queue (largest n

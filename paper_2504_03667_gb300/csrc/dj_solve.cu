@@ -18,6 +18,7 @@
 // The phase logic (what is settled per pass and why it equals Algorithm 1) is
 // in dj_core.cuh.
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "dj_common.cuh"
@@ -669,3 +670,129 @@ SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* p
 }
 
 }  // namespace dj
+
+// ============================================================ allocation-free single solve
+
+// Scratch of dj_sssp_noalloc: the grid engine's control words, per-CTA
+// partials and candidate lists, in a fixed array that exists on every GPU
+// that loads this library (until the process exits).  In host code the name
+// `g_noalloc_scratch` is only a stand-in for the device object; its device
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace dj {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // 4 MiB
+constexpr size_t kNoAllocCtlBytes = 256;                   // barrier + candidate counters (zeroed per call)
+constexpr size_t kNoAllocWordBytes = 64;                   // error bits + phase count (zeroed per call)
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+  bool ready = false;
+  uint8_t* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  int coop = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+// One-time set-up for the current device: device attributes and the scratch
+// array's device address.  Neither allocates device memory.
+int noalloc_setup(NoAllocDevice** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(DJ_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(scratch array)");
+    int major = 0;
+    if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess)
+      return cuda_error(e, "cudaDeviceGetAttribute");
+    if (major < 10) return set_error(DJ_EUNSUPPORTED, "this library targets sm_103a (Blackwell) devices");
+    d.scratch = static_cast<uint8_t*>(ptr);
+    d.ready = true;
+  }
+  *out = &d;
+  return DJ_OK;
+}
+
+}  // namespace
+
+}  // namespace dj
+
+using namespace dj;
+
+// One solve on the grid engine without any device allocation: see dj.h.
+extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream) {
+  clear_error();
+  if (!g || !dist || !pred) return set_error(DJ_EINVAL, "NULL argument");
+  if (source < 0 || source >= g->n) return set_error(DJ_EINVAL, "source outside [0, n)");
+  NoAllocDevice* dv = nullptr;
+  if (int rc = noalloc_setup(&dv)) return rc;
+  if (!dv->coop) return set_error(DJ_EUNSUPPORTED, "device lacks cooperative launch");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  const int nvec_total = g->pitch / 4;
+  const int G = std::min(dv->num_sms, nvec_total);
+  const int nwarps = kGridThreads / 32;
+  const int nvec_cta = (nvec_total + G - 1) / G;
+  Layout L;
+  if (int rc = make_layout(nvec_cta, nwarps, 1, 2, g->pitch, static_cast<size_t>(dv->max_smem_optin) - 1024, &L))
+    return rc;
+  const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
+  const size_t cand_bytes = static_cast<size_t>(2) * g->pitch * sizeof(uint2);
+  const size_t need = kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes + cand_bytes;
+  if (need > kNoAllocScratchBytes)
+    return set_error(DJ_EINVAL, "graph too large for dj_sssp_noalloc: it needs " + std::to_string(need) +
+                                    " bytes of scratch and the fixed array holds " +
+                                    std::to_string(kNoAllocScratchBytes) + " (n up to about 261000)");
+  void* fn = grid_kernel_for(L.V);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
+
+  uint8_t* ws = dv->scratch;
+  // the counters and status words must start at zero; dist[source] = -1 until the solve completes
+  e = cudaMemsetAsync(ws, 0, kNoAllocCtlBytes + kNoAllocWordBytes, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(scratch)");
+  e = cudaMemsetAsync(dist + source, 0xFF, sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(dist[source])");
+
+  GridParams p;
+  p.W = g->W;
+  p.minout = g->minout;
+  p.dist_out = dist;
+  p.pred_out = pred;
+  p.ctl = reinterpret_cast<uint32_t*>(ws);
+  p.words = reinterpret_cast<uint32_t*>(ws + kNoAllocCtlBytes);
+  p.partials = reinterpret_cast<uint4*>(ws + kNoAllocCtlBytes + kNoAllocWordBytes);
+  p.cand = reinterpret_cast<uint2*>(ws + kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes);
+  p.pitch = g->pitch;
+  p.timeout_ns = 2000000000LL;
+  p.n = g->n;
+  p.nvec_total = nvec_total;
+  p.source = source;
+  p.plain = 0;
+  p.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
+  p.span = host_span_for(static_cast<uint32_t>(g->n));
+  p.cand_cap = static_cast<uint32_t>(g->pitch);
+  p.swcap = L.swcap;
+  p.rgs_cap = L.rgs_cap;
+  p.skip_cta = -1;
+  p.list_cap = L.list_cap;
+  p.depth = L.depth;
+  p.rowcap = L.rowcap;
+  p.trace_cap = 0;
+  p.trace = nullptr;
+  void* args[] = {&p};
+  e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
+  return DJ_OK;
+}

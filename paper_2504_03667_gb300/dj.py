@@ -96,6 +96,7 @@ SIGNATURES = {
     "dj_sssp": (_INT, [_P, _I32, _P, _P, _U64]),
     "dj_sssp_ex": (_INT, [_P, _I32, _P, _P, ctypes.POINTER(dj_solve_opts), _U64]),
     "dj_sssp_host": (_INT, [_P, _I32, _P, _P, _U64]),
+    "dj_sssp_noalloc": (_INT, [_P, _I32, _P, _P, _U64]),
     "dj_sync": (_INT, [_U64]),
     "dj_last_phases": (_INT, []),
     "dj_sssp_batch": (_INT, [_P, _P, _I32, _P, _P, _U64]),
@@ -302,6 +303,11 @@ def dj_sssp_host(g, source: int, dist_host=None, pred_host=None, stream=None):
 
     _check(load_library().dj_sssp_host(_gh(g), int(source), hp(dist_host), hp(pred_host), _stream(stream)))
     return dist_host, pred_host
+
+
+def dj_sssp_noalloc(g, source: int, dist, pred, stream=None):
+    """Solve without allocating device memory (fixed scratch array in the library)."""
+    _check(load_library().dj_sssp_noalloc(_gh(g), int(source), _dptr(dist), _dptr(pred), _stream(stream)))
 
 
 def dj_sync(stream=None):
