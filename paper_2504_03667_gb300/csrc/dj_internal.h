@@ -91,8 +91,21 @@ struct ClusterPlan {
   int rowcap = 0;
   uint32_t* words = nullptr;
 };
-int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan);
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve = false);
 int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st);
+
+// The serving request ring as the persistent kernel sees it (device-usable
+// addresses of mapped pinned host memory, plus the device-side head).
+struct ServeRing {
+  const SolveDesc* ring;
+  const uint32_t* tail;
+  const uint32_t* stop;
+  uint32_t* done;
+  uint32_t* head;
+  uint32_t cap_mask;
+  int64_t idle_ns;
+};
+int run_serve_kernel(const ClusterPlan& plan, const ServeRing& r, cudaStream_t st);
 int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters);
 bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl);
 

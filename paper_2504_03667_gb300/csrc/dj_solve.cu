@@ -230,12 +230,70 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
 
 // ============================================================ cluster engine
 
-struct ClusterParams {
+// Where the cluster engine gets its solves.  fetch() and complete() run on
+// thread 0 of cluster rank 0 only.
+struct BatchJobs {
   const SolveDesc* descs;
   uint32_t* queue;  // [0] next solve index (zeroed before launch)
+  int32_t k;
+  __device__ bool fetch(uint32_t* job) const {
+    *job = atomicAdd(queue, 1u);
+    return *job < static_cast<uint32_t>(k);
+  }
+  __device__ SolveDesc desc(uint32_t job) const { return descs[job]; }
+  __device__ void complete(uint32_t) const {}
+};
+
+// Serving: requests arrive in a ring of descriptors in mapped pinned host
+// memory.  The host publishes request r by writing ring[r % cap] and then
+// tail = r + 1 (release); a cluster claims r by advancing the device-side head
+// with a CAS, and reports completion with done[r % cap] = r + 1 (release,
+// system scope).  Waiting for work is bounded: after idle_ns without a
+// request, or once the host sets *stop, fetch() returns false and the kernel
+// exits (the host relaunches it when requests come again).
+struct ServeJobs {
+  const SolveDesc* ring;  // mapped host memory, cap entries
+  const uint32_t* tail;   // mapped host memory
+  const uint32_t* stop;   // mapped host memory
+  uint32_t* done;         // mapped host memory, cap entries
+  uint32_t* head;         // device memory
+  uint32_t cap_mask;
+  int64_t idle_ns;
+  __device__ bool fetch(uint32_t* job) const {
+    uint64_t t0 = global_ns();
+    for (;;) {
+      if (ld_acquire_sys(stop)) return false;
+      const uint32_t h = ld_relaxed_gpu(head);
+      const uint32_t t = ld_acquire_sys(tail);
+      if (static_cast<int32_t>(t - h) > 0) {
+        if (atomicCAS(head, h, h + 1) == h) {
+          *job = h;
+          return true;
+        }
+        continue;
+      }
+      if (static_cast<int64_t>(global_ns() - t0) > idle_ns) return false;
+      __nanosleep(256);
+    }
+  }
+  __device__ SolveDesc desc(uint32_t job) const {
+    const SolveDesc* src = ring + (job & cap_mask);
+    SolveDesc d;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(&d);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d4[i] = __ldcv(s4 + i);
+    return d;
+  }
+  __device__ void complete(uint32_t job) const {
+    __threadfence_system();
+    st_release_sys(done + (job & cap_mask), job + 1);
+  }
+};
+
+struct ClusterParams {
   uint32_t* words;  // per-device words: [0] error bits
   int64_t timeout_ns;
-  int32_t k;
   int32_t swcap;
   int32_t rgs_cap;
   int32_t list_cap;
@@ -243,8 +301,8 @@ struct ClusterParams {
   int32_t rowcap;
 };
 
-template <int V, int U, int THREADS>
-__global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams p) {
+template <int V, int U, int THREADS, class Jobs>
+__global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams p, const Jobs jobs) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BlockScratch sc;
   __shared__ __align__(16) uint4 s_part[2];  // this CTA's published partial, per phase parity
@@ -288,16 +346,19 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
 
   for (;;) {
     // next solve: rank 0 takes it from the queue, every CTA reads it through DSMEM
-    if (rank == 0 && threadIdx.x == 0) s_job = atomicAdd(p.queue, 1u);
+    if (rank == 0 && threadIdx.x == 0) {
+      uint32_t j = 0;
+      s_job = jobs.fetch(&j) ? j : 0xFFFFFFFFu;
+    }
     cluster_sync_all();
     if (threadIdx.x == 0) s_jobl = (rank == 0) ? s_job : ld_dsmem_u32(dsmem_addr(&s_job, 0));
     __syncthreads();
     const uint32_t job = s_jobl;
-    if (job >= static_cast<uint32_t>(p.k)) {
+    if (job == 0xFFFFFFFFu) {
       cluster_sync_all();  // rank 0's s_job stays readable until everyone has it
       return;
     }
-    const SolveDesc d = p.descs[job];
+    const SolveDesc d = jobs.desc(job);
     const int nvec_total = static_cast<int>(d.pitch / 4);
     const int v0 = static_cast<int>(static_cast<int64_t>(rank) * nvec_total / C);
     const int v1 = static_cast<int>(static_cast<int64_t>(rank + 1) * nvec_total / C);
@@ -369,6 +430,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       ++phase;
     }
     slice_write_out(s, d.n, d.dist, d.pred);
+    // every CTA's outputs are visible system-wide before rank 0 reports completion
+    __syncthreads();
+    if (threadIdx.x == 0) __threadfence_system();
+    cluster_sync_all();
+    if (rank == 0 && threadIdx.x == 0) jobs.complete(job);
   }
 }
 
@@ -436,9 +502,9 @@ template <int V>
 void* grid_kernel() {
   return reinterpret_cast<void*>(&k_sssp_grid<V, kRowsPerStage, kGridThreads>);
 }
-template <int V>
+template <int V, class Jobs>
 void* cluster_kernel() {
-  return reinterpret_cast<void*>(&k_sssp_cluster<V, kRowsPerStage, kClusterThreads>);
+  return reinterpret_cast<void*>(&k_sssp_cluster<V, kRowsPerStage, kClusterThreads, Jobs>);
 }
 void* grid_kernel_for(int v) {
   switch (v) {
@@ -448,11 +514,11 @@ void* grid_kernel_for(int v) {
   }
   return nullptr;
 }
-void* cluster_kernel_for(int v) {
+void* cluster_kernel_for(int v, bool serve = false) {
   switch (v) {
-    case 1: return cluster_kernel<1>();
-    case 2: return cluster_kernel<2>();
-    case 4: return cluster_kernel<4>();
+    case 1: return serve ? cluster_kernel<1, ServeJobs>() : cluster_kernel<1, BatchJobs>();
+    case 2: return serve ? cluster_kernel<2, ServeJobs>() : cluster_kernel<2, BatchJobs>();
+    case 4: return serve ? cluster_kernel<4, ServeJobs>() : cluster_kernel<4, BatchJobs>();
   }
   return nullptr;
 }
@@ -588,11 +654,11 @@ bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl) {
   return ok;
 }
 
-int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan) {
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve) {
   if (cl.cluster_size < 1 || cl.cluster_size > 16) return set_error(DJ_EINVAL, "cluster size must be 1..16");
   Layout L;
   if (int rc = cluster_layout(max_pitch, cl, &L)) return rc;
-  void* fn = cluster_kernel_for(L.V);
+  void* fn = cluster_kernel_for(L.V, serve);
   if (int rc = prepare_cluster(fn, cl, L.smem)) return rc;
   int Q = cl.clusters;
   if (Q <= 0) {
@@ -601,7 +667,7 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   DevCtx* ctx = nullptr;
   if (int rc = get_ctx(&ctx)) return rc;
   plan->fn = fn;
-  plan->clusters = std::max(1, std::min(Q, std::max(k, 1)));
+  plan->clusters = serve ? std::max(1, Q) : std::max(1, std::min(Q, std::max(k, 1)));
   plan->cluster_size = cl.cluster_size;
   plan->threads = kClusterThreads;
   plan->smem = L.smem;
@@ -614,20 +680,7 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   return DJ_OK;
 }
 
-int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(queue)");
-  ClusterParams p;
-  p.descs = descs_dev;
-  p.queue = queue;
-  p.words = plan.words;
-  p.timeout_ns = 2000000000LL;
-  p.k = k;
-  p.swcap = plan.swcap;
-  p.rgs_cap = plan.rgs_cap;
-  p.list_cap = plan.list_cap;
-  p.depth = plan.depth;
-  p.rowcap = plan.rowcap;
+static int launch_plan(const ClusterPlan& plan, void** args, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(plan.clusters * plan.cluster_size));
   cfg.blockDim = dim3(static_cast<unsigned>(plan.threads));
@@ -640,10 +693,47 @@ int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  void* args[] = {&p};
-  e = cudaLaunchKernelExC(&cfg, plan.fn, args);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, plan.fn, args);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchKernelEx(cluster engine)");
   return DJ_OK;
+}
+
+static ClusterParams params_of(const ClusterPlan& plan) {
+  ClusterParams p;
+  p.words = plan.words;
+  p.timeout_ns = 2000000000LL;
+  p.swcap = plan.swcap;
+  p.rgs_cap = plan.rgs_cap;
+  p.list_cap = plan.list_cap;
+  p.depth = plan.depth;
+  p.rowcap = plan.rowcap;
+  return p;
+}
+
+int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(queue)");
+  ClusterParams p = params_of(plan);
+  BatchJobs jobs;
+  jobs.descs = descs_dev;
+  jobs.queue = queue;
+  jobs.k = k;
+  void* args[] = {&p, &jobs};
+  return launch_plan(plan, args, st);
+}
+
+int run_serve_kernel(const ClusterPlan& plan, const ServeRing& r, cudaStream_t st) {
+  ClusterParams p = params_of(plan);
+  ServeJobs jobs;
+  jobs.ring = r.ring;
+  jobs.tail = r.tail;
+  jobs.stop = r.stop;
+  jobs.done = r.done;
+  jobs.head = r.head;
+  jobs.cap_mask = r.cap_mask;
+  jobs.idle_ns = r.idle_ns;
+  void* args[] = {&p, &jobs};
+  return launch_plan(plan, args, st);
 }
 
 int launch_cluster(const SolveDesc* descs_dev, int32_t k, int32_t /*max_n*/, int32_t max_pitch, uint32_t* queue,
