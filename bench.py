@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--reference-budget-s", type=float, default=90.0)
     ap.add_argument("--soak-s", type=float, default=1.0, help="untimed load before warm-up (clock sampling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch / plain-form / e2e side measurements")
+    ap.add_argument("--trace", action="store_true", help="print the per-phase device timeline of one solve and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -230,6 +231,9 @@ def main():
 
     def step(i):
         dj.dj_sssp(g, int(srcs[i % 64]), dist_t, pred_t, stream)
+
+    if args.trace:
+        return print_trace(dj, torch, g, int(srcs[0]), n, stream)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -270,20 +274,11 @@ def main():
     per_launch_s = (ms_total / 1e3) / args.steps
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = _peaks()
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "k_sssp_grid_dense_n16384_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                tj = json.load(f)
-            if tj.get("kernel_source_hash") == _kernel_hash():
-                traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic, traffic_note = _traffic(n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                 "frac_of_8tbs": achieved / 8000.0, "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": "k_sssp_grid"}
+                "kernel": "k_sssp_grid", "traffic_note": traffic_note}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -321,6 +316,24 @@ def main():
         dist.destroy_process_group()
 
 
+def _traffic(n: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_sssp_grid_dense_n8192_traffic.txt")
+    try:
+        kv = {}
+        for ln in open(path):
+            if ":" in ln and not ln.startswith("#"):
+                k, v = ln.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != _kernel_hash():
+            return None, "kernel changed since the ncu capture"
+        base_n = int(kv["n"])
+        per = int(kv["dram_bytes_per_launch"])
+        return per * (n / base_n) ** 2, f"ncu dram__bytes_read+write at n={base_n}, scaled by n^2"
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture"
+
+
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -328,6 +341,25 @@ def _kernel_hash() -> str:
         with open(os.path.join(ROOT, "paper_2504_03667_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def print_trace(dj, torch, g, source: int, n: int, stream):
+    """Per-phase timeline of one grid-engine solve (CTA 0's %globaltimer stamps)."""
+    tr = torch.zeros(4 * 4096, dtype=torch.int64, device="cuda")
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = torch.empty_like(d)
+    for _ in range(3):
+        dj.dj_sssp(g, source, d, p, stream)
+    dj.dj_sssp_ex(g, source, d, p, dj.make_solve_opts(engine=dj.DJ_ENGINE_GRID, trace=tr), stream)
+    dj.dj_sync(stream)
+    phases = dj.dj_last_phases()
+    t = tr.cpu().numpy().reshape(-1, 4)[: phases + 1]
+    rows = []
+    for i in range(phases):
+        rows.append({"phase": i, "rows": int(t[i, 3]), "stage_us": (t[i, 1] - t[i, 0]) / 1e3,
+                     "relax_us": (t[i, 2] - t[i, 1]) / 1e3, "merge_publish_barrier_us": (t[i + 1, 0] - t[i, 2]) / 1e3,
+                     "relax_gbs": int(t[i, 3]) * n * 4 / max(t[i, 2] - t[i, 1], 1)})
+    print(json.dumps({"phases": phases, "total_us": (t[phases, 0] - t[0, 0]) / 1e3, "per_phase": rows}), flush=True)
 
 
 def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
@@ -424,7 +456,57 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
                     "phase_single_launch_value": single_rate, "vs_phase_single_launch": batch_rate / single_rate}
     b.free()
     bg.free()
+    out["serve"] = serving_measurement(dj, torch, graphgen, stream)
     return out
+
+
+def serving_measurement(dj, torch, graphgen, stream) -> dict:
+    """64 resident graphs (n log-uniform in [512, 16384], p uniform in [0.01, 0.5]),
+    10000 Poisson requests: saturation throughput, then latency at ~70 % load."""
+    spec = graphgen.WORKLOADS["serving_64graphs_10000req"]
+    probe = graphgen.serving_trace(spec["graphs"], spec["requests"], 1.0, spec["seed"])
+    graphs = []
+    t0 = time.perf_counter()
+    for gi in range(spec["graphs"]):
+        e = graphgen.bernoulli(int(probe.graph_n[gi]), float(probe.graph_p[gi]), spec["wlo"], spec["whi"],
+                               int(probe.graph_seed[gi]))
+        graphs.append(dj.dj_load_edges(e.n, e.src, e.dst, e.w, False))
+        del e
+    setup_s = time.perf_counter() - t0
+    resident = sum(int(dj.dj_graph_get_info(g)["bytes"]) for g in graphs)
+    opts = dj.make_serve_opts(max_slots=512)
+    # saturation: every request already waiting at t = 0
+    zero = np.zeros(spec["requests"])
+    sat = dj.dj_serve(graphs, probe.req_graph, probe.req_source, zero, opts=opts)
+    rate = 0.7 * sat["solves_per_s"]
+    tr = graphgen.serving_trace(spec["graphs"], spec["requests"], rate, spec["seed"])
+    live = dj.dj_serve(graphs, tr.req_graph, tr.req_source, tr.req_arrival_s, opts=opts)
+    # the plain form on a sample of the same requests: one literal-Algorithm-1 launch each, synchronous
+    o = dj.make_solve_opts(mode=dj.DJ_MODE_PLAIN)
+    sample = list(range(0, spec["requests"], spec["requests"] // 16))[:16]
+    bufs = {}
+    t_plain = 0.0
+    for r in sample:
+        g = graphs[int(tr.req_graph[r])]
+        n = int(dj.dj_graph_get_info(g)["n"])
+        if n not in bufs:
+            bufs[n] = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+        d, p = bufs[n]
+        t1 = time.perf_counter()
+        dj.dj_sssp_ex(g, int(tr.req_source[r]), d, p, o, stream)
+        dj.dj_sync(stream)
+        t_plain += time.perf_counter() - t1
+    plain_rate = len(sample) / t_plain
+    for g in graphs:
+        g.free()
+    return {"workload": "serving_64graphs_10000req", "graphs": spec["graphs"], "requests": spec["requests"],
+            "resident_bytes": resident, "setup_s": setup_s,
+            "saturation_solves_per_s": sat["solves_per_s"],
+            "rate_per_s": rate, "solves_per_s": live["solves_per_s"], "p50_us": live["p50_us"],
+            "p90_us": live["p90_us"], "p99_us": live["p99_us"], "max_us": live["max_us"],
+            "deferred_requests": live["rejected"], "kernel_launches": live["kernel_launches"],
+            "plain_form_value": plain_rate, "vs_plain_form": live["solves_per_s"] / plain_rate,
+            "plain_form_sample": f"{len(sample)} requests of the trace, one plain launch each, synchronous"}
 
 
 if __name__ == "__main__":
