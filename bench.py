@@ -345,7 +345,7 @@ def _kernel_hash() -> str:
 
 def print_trace(dj, torch, g, source: int, n: int, stream):
     """Per-phase timeline of one grid-engine solve (CTA 0's %globaltimer stamps)."""
-    tr = torch.zeros(4 * 4096, dtype=torch.int64, device="cuda")
+    tr = torch.zeros(8 * 4096, dtype=torch.int64, device="cuda")
     d = torch.empty(n, dtype=torch.int32, device="cuda")
     p = torch.empty_like(d)
     for _ in range(3):
@@ -353,13 +353,18 @@ def print_trace(dj, torch, g, source: int, n: int, stream):
     dj.dj_sssp_ex(g, source, d, p, dj.make_solve_opts(engine=dj.DJ_ENGINE_GRID, trace=tr), stream)
     dj.dj_sync(stream)
     phases = dj.dj_last_phases()
-    t = tr.cpu().numpy().reshape(-1, 4)[: phases + 1]
+    t = tr.cpu().numpy().reshape(-1, 8)[: phases + 1]
+    names = ["publish_us", "arrive_us", "barrier_wait_us", "decision_us", "relax_us", "commit_us"]
     rows = []
     for i in range(phases):
-        rows.append({"phase": i, "rows": int(t[i, 3]), "stage_us": (t[i, 1] - t[i, 0]) / 1e3,
-                     "relax_us": (t[i, 2] - t[i, 1]) / 1e3, "merge_publish_barrier_us": (t[i + 1, 0] - t[i, 2]) / 1e3,
-                     "relax_gbs": int(t[i, 3]) * n * 4 / max(t[i, 2] - t[i, 1], 1)})
-    print(json.dumps({"phases": phases, "total_us": (t[phases, 0] - t[0, 0]) / 1e3, "per_phase": rows}), flush=True)
+        d_ = {"phase": i, "candidates": int(t[i, 7])}
+        for k, nm in enumerate(names):
+            d_[nm] = (t[i, k + 1] - t[i, k]) / 1e3
+        d_["relax_gbs_upper"] = int(t[i, 7]) * n * 4 / max(t[i, 5] - t[i, 4], 1)
+        rows.append(d_)
+    sums = {nm: sum(r[nm] for r in rows) for nm in names}
+    print(json.dumps({"phases": phases, "total_us": (t[phases, 4] - t[0, 0]) / 1e3, "sums_us": sums,
+                      "per_phase": rows if phases <= 64 else rows[:8]}), flush=True)
 
 
 def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:

@@ -64,6 +64,7 @@ typedef struct dj_graph_info {
   int32_t device;        /* CUDA device holding the matrix */
   const int32_t* matrix; /* device pointer: n rows x pitch int32, row-major; columns >= n hold DJ_INF */
   const int32_t* minout; /* device pointer: n int32, min finite off-diagonal weight of row u (DJ_INF if none) */
+  const int32_t* minin;  /* device pointer: n int32, min finite off-diagonal weight of column v (DJ_INF if none) */
   uint64_t bytes;        /* device bytes owned by the graph */
 } dj_graph_info;
 
@@ -129,11 +130,17 @@ typedef struct dj_solve_opts {
   int64_t timeout_ns;     /* limit of every in-kernel wait, 0 = 2 s */
   int32_t debug_skip_cta; /* testing only: this CTA leaves before the first grid barrier (-1 = none) */
   int32_t trace_cap;      /* grid engine profiling: entries of `trace` (0 = no trace) */
-  uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 records 4 words
-                             (%globaltimer at the phase's barrier exit, after staging, after the
-                             relaxation, and the settled-row count); unused entries are left as is */
-  int32_t reserved[2];
+  uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 records 8 words:
+                             %globaltimer at publish start, publish end, barrier arrival, barrier
+                             exit, decision end, relaxation end, commit end, then the phase's
+                             candidate count; unused entries are left as is */
+  int32_t settle;         /* phase mode's settle bounds: DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN */
+  int32_t reserved[1];
 } dj_solve_opts;
+
+#define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only */
+#define DJ_SETTLE_OUT 1    /* OUT bound only (nodes settled in Algorithm 1's visit order) */
+#define DJ_SETTLE_OUT_IN 2 /* OUT and IN bounds; falls back to OUT when some weight is 0 */
 
 /* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */
 void dj_solve_opts_init(dj_solve_opts* opts);

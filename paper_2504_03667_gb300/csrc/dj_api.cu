@@ -106,7 +106,8 @@ static int solve_cluster_single(const dj_graph* g, int32_t source, int32_t* dist
   ClusterLaunch cl;
   cl.cluster_size = o.cluster_size > 0 ? o.cluster_size : default_cluster_size(g->n);
   cl.clusters = 1;
-  const SolveDesc d = make_desc(g, source, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0);
+  SolveDesc d = make_desc(g, source, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0);
+  if (o.settle == DJ_SETTLE_OUT) d.use_in = 0;
   uint8_t* ws = nullptr;
   cudaError_t e = cudaMallocAsync(&ws, 128, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(cluster workspace)");
@@ -132,6 +133,7 @@ extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int3
   dj_solve_opts_init(&o);
   if (opts) o = *opts;
   if (o.mode < DJ_MODE_AUTO || o.mode > DJ_MODE_PLAIN) return set_error(DJ_EINVAL, "unknown mode");
+  if (o.settle < DJ_SETTLE_AUTO || o.settle > DJ_SETTLE_OUT_IN) return set_error(DJ_EINVAL, "unknown settle bounds");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int engine = o.engine;
   if (engine == DJ_ENGINE_AUTO) engine = g->n >= kGridMinN ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;

@@ -28,6 +28,14 @@
 //     relaxation needs no visited test (it is kept in the selection only).
 //   - L is capped at m + 2^(32 - bits(n)) so (dist[u] - m, u) packs into 32
 //     bits; a smaller L only shrinks S, and S always contains a.
+//   - With every off-diagonal weight >= 1, the "IN" criterion of the same
+//     paper also settles v when dist[v] <= m + minin[v] (minin: the smallest
+//     weight into v): the last edge of a shorter path would have to leave an
+//     unvisited node, whose distance is >= m.  Such nodes are final but may be
+//     settled before Algorithm 1 would visit them, so commits compare the full
+//     key (candidate, dist[u], u) with the stored (dist[v], dist[pred[v]],
+//     pred[v]); the surviving pred is the u of smallest (dist[u], u) offering
+//     dist[v], which is the one Algorithm 1 keeps when weights are >= 1.
 // All sums are unsigned 32-bit: dist <= INF and G <= INF, so dist + G never
 // wraps, and an INF entry yields a candidate >= INF that never improves.
 #pragma once
@@ -49,7 +57,9 @@ struct BlockScratch {
 struct Slice {
   uint32_t* dist;
   int32_t* pred;
+  uint32_t* pdist;   // dist of pred[v] (the key's second field)
   uint32_t* minout;
+  uint32_t* minin;
   uint8_t* vis;
   int c0;    // first column (node id) of the slice, a multiple of 4
   int sw;    // columns in the slice, a multiple of 4
@@ -58,20 +68,27 @@ struct Slice {
 
 // Global decision of one phase.
 struct Decision {
-  uint32_t m;  // smallest unvisited dist (kInf: done)
-  uint32_t a;  // its node (smallest index on ties)
-  uint32_t L;  // settle bound: S = {unvisited v : dist[v] < L} u {a}
+  uint32_t m;     // smallest unvisited dist (kInf: done)
+  uint32_t a;     // its node (smallest index on ties)
+  uint32_t L;     // OUT bound: unvisited v with dist[v] < L are settled
+  uint32_t span;  // packing span 2^(32 - bits(n))
+  uint32_t use_in;
 };
 
+// IN key of a node: dist - minin (saturating); settled by IN when <= m.
+__device__ __forceinline__ uint32_t in_key(uint32_t d, uint32_t minin) { return d > minin ? d - minin : 0u; }
+
 __device__ __forceinline__ void slice_init(const Slice& s, int n, int source, const int32_t* minout_g,
-                                           bool need_minout) {
+                                           const int32_t* minin_g, bool need_minout, bool need_minin) {
   for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
     int v = s.c0 + j;
     bool real = v < n;
     s.dist[j] = (real && v == source) ? 0u : kInf;
+    s.pdist[j] = (real && v == source) ? 0u : kInf;
     s.pred[j] = -1;
     s.vis[j] = real ? 0 : 1;  // padding columns never take part
     s.minout[j] = (real && need_minout) ? static_cast<uint32_t>(__ldg(minout_g + v)) : kInf;
+    s.minin[j] = (real && need_minin) ? static_cast<uint32_t>(__ldg(minin_g + v)) : kInf;
   }
 }
 
@@ -101,69 +118,92 @@ __device__ __forceinline__ void block_min2(uint64_t& k, uint32_t& l, BlockScratc
   __syncthreads();
 }
 
-// Local partial of step 1: returns the slice's argmin key (dist << 32 | v) and
-// its settle bound L_c (already capped), and writes the candidates
-// {unvisited v : dist[v] < L_c} u {argmin} as (v, dist[v]) to `out`
-// (compacted, in no particular order).  Returns the candidate count.  `plain` publishes
-// the argmin only.
-__device__ __forceinline__ int slice_publish(const Slice& s, uint32_t span, bool plain, uint2* out,
-                                             uint64_t* key_out, uint32_t* Lc_out, BlockScratch* sc) {
-  uint64_t key = kNoKey;
-  uint32_t lc = 0xFFFFFFFFu;
-  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
-    if (!s.vis[j]) {
-      uint32_t d = s.dist[j];
-      uint64_t kj = (static_cast<uint64_t>(d) << 32) | static_cast<uint32_t>(s.c0 + j);
-      key = kj < key ? kj : key;
-      lc = min(lc, d + s.minout[j]);  // <= 2^32 - 2: no wrap
-    }
-  }
-  block_min2(key, lc, sc);
+// Settle bound of a CTA from its raw partial: no bound when nothing reachable
+// is left; the argmin alone in plain mode; otherwise min(L_c, m + span, INF).
+__device__ __forceinline__ uint32_t cap_bound(uint64_t key, uint32_t lc, uint32_t span, bool plain) {
   const uint32_t mc = static_cast<uint32_t>(key >> 32);
-  const uint32_t ac = static_cast<uint32_t>(key);
-  uint32_t Lc;
-  if (mc >= kInf) {
-    Lc = 0xFFFFFFFFu;  // nothing reachable left in this slice: no bound
-  } else if (plain) {
-    Lc = mc;  // only the argmin itself
-  } else {
-    Lc = min(min(lc, mc + span), kInf);
+  if (mc >= kInf) return 0xFFFFFFFFu;
+  if (plain) return mc;
+  return min(min(lc, mc + span), kInf);
+}
+
+// Per-thread part of a slice's partial: argmin key (dist << 32 | v) and
+// min(dist + minout) over the unvisited columns this thread visits.
+__device__ __forceinline__ void column_partial(const Slice& s, int j, uint64_t& key, uint32_t& lc) {
+  if (!s.vis[j]) {
+    const uint32_t d = s.dist[j];
+    const uint64_t kj = (static_cast<uint64_t>(d) << 32) | static_cast<uint32_t>(s.c0 + j);
+    key = kj < key ? kj : key;
+    lc = min(lc, d + s.minout[j]);  // <= 2^32 - 2: no wrap
   }
-  *key_out = key;
+}
+
+__device__ __forceinline__ void slice_partial(const Slice& s, uint64_t& key, uint32_t& lc) {
+  key = kNoKey;
+  lc = 0xFFFFFFFFu;
+  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) column_partial(s, j, key, lc);
+}
+
+// Step 1: reduce the per-thread partials to the slice's (key, L_c) and append
+// the candidates {unvisited v : dist[v] < L_c} u {argmin} as (v, dist[v]) to
+// `out` (order irrelevant: the relaxation keys are order-free).  sc->cnt[32]
+// must be zero on entry.  Returns the count; all threads get key, Lc, count.
+__device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bool plain, bool use_in,
+                                               uint64_t key_t, uint32_t lc_t, uint4* out, BlockScratch* sc,
+                                               uint64_t* key_out, uint32_t* Lc_out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  uint64_t k = warp_min_u64(key_t);
+  uint32_t l = warp_min_u32(lc_t);
+  if (lane == 0) {
+    sc->r64[w] = k;
+    sc->r32[w] = l;
+  }
+  __syncthreads();
+  k = kNoKey;
+  l = 0xFFFFFFFFu;
+  for (int i = 0; i < nw; ++i) {  // every thread reduces the warp results itself
+    const uint64_t x = sc->r64[i];
+    k = x < k ? x : k;
+    l = min(l, sc->r32[i]);
+  }
+  const uint32_t Lc = cap_bound(k, l, span, plain);
+  const uint32_t ac = static_cast<uint32_t>(k);
+  const uint32_t mc = static_cast<uint32_t>(k >> 32);
+  *key_out = k;
   *Lc_out = Lc;
-  if (mc >= kInf) return 0;
-  // append {unvisited, dist < Lc} u {argmin}: one shared-memory atomic per warp
-  // (the order of the list is irrelevant: the relaxation keys are order-free)
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) sc->cnt[32] = 0;
-  __syncthreads();
-  for (int j0 = 0; j0 < s.sw; j0 += blockDim.x) {
-    const int j = j0 + threadIdx.x;
-    bool p = false;
-    uint32_t d = 0;
-    if (j < s.sw && !s.vis[j]) {
-      d = s.dist[j];
-      p = d < Lc || static_cast<uint32_t>(s.c0 + j) == ac;
-    }
-    const uint32_t bal = __ballot_sync(0xffffffffu, p);
-    if (bal) {
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (p) out[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(static_cast<uint32_t>(s.c0 + j), d);
+  if (mc < kInf) {
+    for (int j0 = 0; j0 < s.sw; j0 += blockDim.x) {
+      const int j = j0 + threadIdx.x;
+      bool p = false;
+      uint32_t d = 0, ik = 0;
+      if (j < s.sw && !s.vis[j]) {
+        d = s.dist[j];
+        ik = in_key(d, s.minin[j]);
+        // a superset of this phase's settled nodes: the global m is <= mc
+        p = d < Lc || static_cast<uint32_t>(s.c0 + j) == ac ||
+            (use_in && !plain && d < kInf && ik <= mc && d - mc < span);
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, p);
+      if (bal) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (p) out[pos + __popc(bal & ((1u << lane) - 1u))] = make_uint4(static_cast<uint32_t>(s.c0 + j), d, ik, 0u);
+      }
     }
   }
   __syncthreads();
-  const int total = static_cast<int>(sc->cnt[32]);
-  __syncthreads();
-  return total;
+  return static_cast<int>(sc->cnt[32]);
 }
 
 // Combine per-CTA partials (key, Lc) into the phase decision.
-__device__ __forceinline__ Decision make_decision(uint64_t key, uint32_t Lc, uint32_t span, bool plain) {
+__device__ __forceinline__ Decision make_decision(uint64_t key, uint32_t Lc, uint32_t span, bool plain,
+                                                 bool use_in) {
   Decision d;
   d.m = static_cast<uint32_t>(key >> 32);
   d.a = static_cast<uint32_t>(key);
+  d.span = span;
+  d.use_in = (use_in && !plain) ? 1u : 0u;
   if (d.m >= kInf) {
     d.m = kInf;
     d.L = 0;
@@ -175,15 +215,10 @@ __device__ __forceinline__ Decision make_decision(uint64_t key, uint32_t Lc, uin
   return d;
 }
 
-__device__ __forceinline__ bool in_settled(uint32_t u, uint32_t du, const Decision& D) {
-  return du < D.L || u == D.a;
-}
-
-// Step 3 for the CTA's own nodes: mark the settled ones visited.
-__device__ __forceinline__ void slice_mark(const Slice& s, const Decision& D) {
-  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
-    if (!s.vis[j] && in_settled(static_cast<uint32_t>(s.c0 + j), s.dist[j], D)) s.vis[j] = 1;
-  }
+// Settled this phase: below the OUT bound, the argmin itself, or (weights >= 1)
+// proven final by the IN bound while still packable.
+__device__ __forceinline__ bool in_settled(uint32_t u, uint32_t du, uint32_t ik, const Decision& D) {
+  return du < D.L || u == D.a || (D.use_in && du < kInf && ik <= D.m && du - D.m < D.span);
 }
 
 // Thread tile of the relaxation: warps split into `wpr` column chunks of
@@ -206,74 +241,62 @@ __device__ __forceinline__ Tile make_tile(int nvec, int rgs_cap) {
   return t;
 }
 
-// Settled rows are staged in shared memory as their 32-bit tie-break word
-// tb = ((dist[u] - m) << bits_u) | u  (dist[u] = m + (tb >> bits_u)).
-// stage_list appends the settled entries among candidates [begin, end) of
-// `get` to `list` (order irrelevant) and returns the new count.  Ends synced.
-template <class Get>
-__device__ __forceinline__ int stage_list(const Get& get, int begin, int end, const Decision& D, uint32_t bits_u,
-                                          uint32_t* list, int base, BlockScratch* sc) {
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) sc->cnt[32] = static_cast<uint32_t>(base);
-  __syncthreads();
-  constexpr int K = 4;
-  for (int i0 = begin; i0 < end; i0 += K * blockDim.x) {
-    uint2 e[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int i = i0 + k * blockDim.x + threadIdx.x;
-      e[k] = i < end ? get(i) : make_uint2(0xffffffffu, kInf);
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool p = e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, D);
-      const uint32_t bal = __ballot_sync(0xffffffffu, p);
-      if (bal) {
-        uint32_t pos = 0;
-        if (lane == 0) pos = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (p) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((e[k].y - D.m) << bits_u) | e[k].x;
-      }
-    }
-  }
-  __syncthreads();
-  const int total = static_cast<int>(sc->cnt[32]);
-  __syncthreads();
-  return total;
-}
-
 // A warp's ring of `depth` stages x U row slots in shared memory, filled by
 // 1-D TMA bulk copies (one per row) that complete on the stage's mbarrier.
 // Only this warp issues into and reads from its ring, so no other warp ever
 // waits on it.  `gt` counts the warp's stages over the whole kernel: stage g
-// uses slot g % depth and waits for parity (g / depth) & 1 (depth = 2^lg).
+// uses slot g % depth and waits for parity (g / depth) & 1.
 struct Ring {
   uint8_t* buf;
   uint64_t* bar;
-  uint32_t lg;        // log2(depth)
+  uint32_t depth;
+  uint32_t srows;     // rows per stage (<= U)
   uint32_t rowbytes;  // bytes of this warp's column chunk of one row (0: idle warp)
   uint32_t gt;
 };
 
 // Per-column running best of one relaxation pass: candidate value bc and its
-// tie-break word bt.  It starts at (dist[v], 0): a candidate that does not beat
-// the current dist can never be committed, and a tie with it never wins.
+// tie-break word bt.  It starts at the column's stored key: (dist[v], the tie
+// word of pred[v] relative to this phase), so a candidate commits only if it
+// is lexicographically smaller -- a shorter distance, or the same distance
+// offered by a node of smaller (dist, index).
 template <int V>
 struct Best {
   uint32_t bc[V][4];
   uint32_t bt[V][4];
 };
 
+// Tie word of column j's stored pred in this phase's packing: 0 when no
+// candidate of the phase can tie-beat it (pred settled earlier, or the source),
+// all ones when any can (unreached, or the pred's dist is beyond the span).
+// Without the IN bound (some weight is 0, or plain mode) ties never commit:
+// nodes are then settled in Algorithm 1's own order, where strict improvement
+// is exactly its rule, while with zero weights a tie could even come from a
+// node's own diagonal entry.
+__device__ __forceinline__ uint32_t stored_tie(const Slice& s, int j, const Decision& D, uint32_t bits_u) {
+  if (!D.use_in) return 0u;
+  if (s.dist[j] >= kInf) return 0xFFFFFFFFu;
+  const int32_t pr = s.pred[j];
+  if (pr < 0) return 0u;
+  const uint32_t pd = s.pdist[j];
+  if (pd < D.m) return 0u;
+  const uint32_t dd = pd - D.m;
+  if (dd >= D.span) return 0xFFFFFFFFu;
+  return (dd << bits_u) | static_cast<uint32_t>(pr);
+}
+
 template <int V>
-__device__ __forceinline__ void best_init(Best<V>& b, const Slice& s, const Tile& t) {
+__device__ __forceinline__ void best_init(Best<V>& b, const Slice& s, const Tile& t, const Decision& D,
+                                          uint32_t bits_u) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     const int jv = (t.wc * V + k) * 32 + lane;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      b.bc[k][c] = (t.active && jv < s.nvec) ? s.dist[4 * jv + c] : kInf;
-      b.bt[k][c] = 0;
+      const bool on = t.active && jv < s.nvec;
+      b.bc[k][c] = on ? s.dist[4 * jv + c] : kInf;
+      b.bt[k][c] = on ? stored_tie(s, 4 * jv + c, D, bits_u) : 0u;
     }
   }
 }
@@ -285,59 +308,60 @@ __device__ __forceinline__ void best_update(uint32_t c, uint32_t tb, uint32_t& b
   }
 }
 
-// Relax the `cnt` staged rows over this CTA's slice.  Row group rg takes
-// list entries rg, rg + rgs, ...; its column-chunk warp streams those rows'
-// slices through its ring `depth` stages ahead of the arithmetic.  The common
-// case (no lane improves or ties its column) costs four adds, four compares
-// and one vote per row; the exact lexicographic update runs only otherwise.
-template <int V, int U>
-__device__ __forceinline__ bool relax_list(const uint32_t* __restrict__ list, int cnt, const Slice& s, const Tile& t,
-                                           const int32_t* __restrict__ W, int64_t pitch, uint32_t m, uint32_t bits_u,
-                                           Ring& ring, int64_t timeout_ns, Best<V>& best) {
-  if (!t.active || ring.rowbytes == 0) return true;
+// Commit the phase's best key of column `col` if it beats the stored one.
+__device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key, uint32_t tie0, const Decision& D,
+                                           uint32_t bits_u) {
+  const uint32_t c = static_cast<uint32_t>(key >> 32);
+  const uint32_t tb = static_cast<uint32_t>(key);
+  if (c < kInf && (c < s.dist[col] || (c == s.dist[col] && tb < tie0))) {
+    s.dist[col] = c;
+    s.pred[col] = static_cast<int32_t>(tb & ((1u << bits_u) - 1u));
+    s.pdist[col] = D.m + (tb >> bits_u);
+  }
+}
+
+// Relax the settled rows among `total` candidates (u, dist[u], IN key) given by
+// get(i) over this CTA's slice.  Row group rg takes candidates rg, rg + rgs,
+// ... (so every row group gets the same share): 32 at a time, one per lane,
+// a ballot picks the settled ones, and their slices go through the warp's
+// TMA ring in stages of up to U rows, `depth` stages ahead of the arithmetic.
+// The common case (no lane improves or ties its column) costs four adds, four
+// compares and one vote per row; the exact lexicographic update runs only
+// otherwise.  No block-wide barrier is involved.
+template <int V, int U, class Get>
+__device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slice& s, const Tile& t,
+                                           const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
+                                           uint32_t bits_u, Ring& ring, uint32_t* slot_rows, uint32_t* slot_tb,
+                                           int64_t timeout_ns, Best<V>& best) {
+  if (!t.active || ring.rowbytes == 0 || t.rg >= total) return true;
   const int lane = threadIdx.x & 31;
   bool jok[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) jok[k] = (t.wc * V + k) * 32 + lane < s.nvec;
   const uint32_t umask = (1u << bits_u) - 1u;
-  const uint32_t dmask = (1u << ring.lg) - 1u;
-  const int J = t.rg < cnt ? (cnt - t.rg + t.rgs - 1) / t.rgs : 0;
-  const int nst = (J + U - 1) / U;
+  const uint32_t depth = ring.depth;
   const char* colbase = reinterpret_cast<const char*>(W + s.c0) + static_cast<size_t>(t.wc) * V * 32 * 16;
   const int64_t rowstride = pitch * 4;
-  const uint32_t* mylist = list + t.rg;
-  const int rgs = t.rgs;
-  auto issue = [&](int st) {
-    const uint32_t slot = (ring.gt + static_cast<uint32_t>(st)) & dmask;
-    const int rows = min(U, J - st * U);
-    uint64_t* bar = ring.bar + slot;
-    if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(rows) * ring.rowbytes);
-    __syncwarp();
-    if (lane < rows) {
-      const uint32_t u = mylist[(st * U + lane) * rgs] & umask;
-      bulk_g2s(ring.buf + (static_cast<size_t>(slot) * U + lane) * ring.rowbytes,
-               colbase + static_cast<int64_t>(u) * rowstride, ring.rowbytes, bar);
-    }
-  };
-  const int depth = 1 << ring.lg;
-  const int pre = min(depth, nst);
-  for (int st = 0; st < pre; ++st) issue(st);
+  const uint32_t m = D.m;
+  // stage counters, with their slot and parity kept incrementally
+  uint32_t issued = ring.gt, consumed = ring.gt;
+  uint32_t islot = ring.gt % depth;
+  uint32_t cslot = islot, cpar = (ring.gt / depth) & 1u;
   bool ok = true;
-  for (int st = 0; st < nst; ++st) {
-    const uint32_t g = ring.gt + static_cast<uint32_t>(st);
-    const uint32_t slot = g & dmask;
-    const uint32_t parity = (g >> ring.lg) & 1u;
-    if (!mbar_wait_bounded(ring.bar + slot, parity, timeout_ns)) {
+
+  auto consume = [&]() {
+    const uint32_t slot = cslot;
+    if (!mbar_wait_bounded(ring.bar + slot, cpar, timeout_ns)) {
       ok = false;
-      mbar_wait_bounded(ring.bar + slot, parity, timeout_ns);  // drain once more
+      mbar_wait_bounded(ring.bar + slot, cpar, timeout_ns);  // drain once more
     }
-    const int rows = min(U, J - st * U);
-    const uint8_t* sb = ring.buf + static_cast<size_t>(slot) * U * ring.rowbytes + 16 * lane;
-    const uint32_t* lrow = mylist + st * U * rgs;
+    const int rows = static_cast<int>(slot_rows[slot]);
+    const uint8_t* sb = ring.buf + static_cast<size_t>(slot) * ring.srows * ring.rowbytes + 16 * lane;
+    const uint32_t* tbs = slot_tb + slot * U;
 #pragma unroll
     for (int uu = 0; uu < U; ++uu) {
       if (uu < rows) {
-        const uint32_t tb = lrow[uu * rgs];
+        const uint32_t tb = tbs[uu];
         const uint32_t du = m + (tb >> bits_u);
         uint32_t c[V][4];
         bool hit = false;
@@ -365,25 +389,72 @@ __device__ __forceinline__ bool relax_list(const uint32_t* __restrict__ list, in
     }
     __syncwarp();
     fence_proxy_async_smem();  // this slot's reads are done before its next TMA write
-    if (st + depth < nst) issue(st + depth);
+    ++consumed;
+    if (++cslot == depth) {
+      cslot = 0;
+      cpar ^= 1u;
+    }
+  };
+
+  // candidate k of this row group is get(rg + rgs * k); lane l takes k = 32 j + l
+  const int K = (total - t.rg + t.rgs - 1) / t.rgs;
+  auto fetch = [&](int j) -> uint4 {
+    const int k = 32 * j + lane;
+    return k < K ? get(t.rg + t.rgs * k) : make_uint4(0xffffffffu, kInf, kInf, 0u);
+  };
+  uint4 nxt = fetch(0), nxt2 = fetch(1);  // two chunks of candidates in flight
+  for (int j = 0; 32 * j < K; ++j) {
+    const uint4 e = nxt;
+    nxt = nxt2;
+    nxt2 = fetch(j + 2);
+    const bool settled = e.x != 0xffffffffu && in_settled(e.x, e.y, e.z, D);
+    const uint32_t mask = __ballot_sync(0xffffffffu, settled);
+    const int nrows = __popc(mask);
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    const int srows = static_cast<int>(ring.srows);
+    for (int k0 = 0; k0 < nrows; k0 += srows) {
+      if (issued - consumed == depth) consume();
+      const uint32_t slot = islot;
+      const int rows = min(srows, nrows - k0);
+      const bool mine = settled && rank >= k0 && rank < k0 + rows;
+      if (lane == 0) {
+        slot_rows[slot] = static_cast<uint32_t>(rows);
+        mbar_arrive_expect_tx(ring.bar + slot, static_cast<uint32_t>(rows) * ring.rowbytes);
+      }
+      if (mine) slot_tb[slot * U + (rank - k0)] = ((e.y - m) << bits_u) | e.x;
+      __syncwarp();
+      if (mine) {
+        bulk_g2s(ring.buf + (static_cast<size_t>(slot) * ring.srows + (rank - k0)) * ring.rowbytes,
+                 colbase + static_cast<int64_t>(e.x & umask) * rowstride, ring.rowbytes, ring.bar + slot);
+      }
+      ++issued;
+      if (++islot == depth) islot = 0;
+    }
   }
-  ring.gt += static_cast<uint32_t>(nst);
+  while (consumed != issued) consume();
+  ring.gt = issued;
   return ok;
 }
 
-__device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key, uint32_t bits_u) {
-  const uint32_t c = static_cast<uint32_t>(key >> 32);
-  if (c < s.dist[col]) {
-    s.dist[col] = c;
-    s.pred[col] = static_cast<int32_t>(static_cast<uint32_t>(key) & ((1u << bits_u) - 1u));
-  }
-}
-
-// Merge the row groups' bests and commit.  Ends synced.
+// Merge the row groups' bests, then for every column: mark it visited if it
+// was settled this phase (judged on its state before this phase's commit),
+// commit a lexicographically smaller key, and fold the column into this
+// thread's part of the next partial.  Starts with a barrier when row groups
+// must be merged.
 template <int V>
-__device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint64_t* merge, uint32_t bits_u,
-                                             const Best<V>& best) {
+__device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, const Decision& D, uint64_t* merge,
+                                               uint32_t bits_u, const Best<V>& best, uint64_t& key,
+                                               uint32_t& lc) {
   const int lane = threadIdx.x & 31;
+  key = kNoKey;
+  lc = 0xFFFFFFFFu;
+  auto one = [&](int col, uint64_t b) {
+    const uint32_t d = s.dist[col];
+    const uint32_t tie0 = stored_tie(s, col, D, bits_u);
+    if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
+    commit_key(s, col, b, tie0, D, bits_u);
+    column_partial(s, col, key, lc);
+  };
   if (t.rgs == 1) {
     if (t.active) {
 #pragma unroll
@@ -392,11 +463,10 @@ __device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint
         if (jv < s.nvec) {
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            commit_key(s, 4 * jv + c, (static_cast<uint64_t>(best.bc[k][c]) << 32) | best.bt[k][c], bits_u);
+            one(4 * jv + c, (static_cast<uint64_t>(best.bc[k][c]) << 32) | best.bt[k][c]);
         }
       }
     }
-    __syncthreads();
     return;
   }
   if (t.active) {
@@ -417,9 +487,8 @@ __device__ __forceinline__ void merge_commit(const Slice& s, const Tile& t, uint
       const uint64_t x = merge[static_cast<size_t>(r) * s.sw + col];
       b = x < b ? x : b;
     }
-    commit_key(s, col, b, bits_u);
+    one(col, b);
   }
-  __syncthreads();
 }
 
 __device__ __forceinline__ void slice_write_out(const Slice& s, int n, int32_t* dist_out, int32_t* pred_out) {

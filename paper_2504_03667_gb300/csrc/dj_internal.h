@@ -16,7 +16,8 @@ struct dj_graph {
   int32_t wmin = DJ_INF;  // smallest finite off-diagonal weight
   int32_t wmax = 0;       // largest finite off-diagonal weight
   int32_t* W = nullptr;       // n x pitch, row-major
-  int32_t* minout = nullptr;  // n
+  int32_t* minout = nullptr;  // n row minima (then the n column minima, same allocation)
+  int32_t* minin = nullptr;   // n column minima
   uint64_t bytes = 0;
 };
 
@@ -34,7 +35,7 @@ struct SolveDesc {
   uint32_t bits_u;
   uint32_t span;
   int32_t plain;
-  int32_t pad;
+  int32_t use_in;  // settle by the IN bound too (every off-diagonal weight >= 1); minin = minout + n
 };
 static_assert(sizeof(SolveDesc) == 64, "descriptor layout");
 
@@ -86,8 +87,8 @@ struct ClusterPlan {
   size_t smem = 0;
   int swcap = 0;
   int rgs_cap = 0;
-  int list_cap = 0;
   int depth = 0;
+  int srows = 0;
   int rowcap = 0;
   uint32_t* words = nullptr;
 };

@@ -6,7 +6,8 @@
 // built directly in HBM: a vectorised INF fill with a zero diagonal, a scatter
 // of the edges with atomicMin (so a repeated pair keeps its smallest weight,
 // independent of order), and one pass computing each row's smallest finite
-// off-diagonal weight (minout, used by the phase-batched solve).  Rows are
+// off-diagonal weight (minout) and each column's (minin), both used by the
+// phase-batched solve to prove nodes final.  Rows are
 // padded to a multiple of 32 int32 (128 bytes) with INF, the device analogue
 // of the paper's INF padding of Section III-B.
 #include <algorithm>
@@ -87,6 +88,29 @@ __global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   }
 }
 
+// minin[v] = min finite W[u][v], u != v.  A block covers 256 columns x kColRows
+// rows (coalesced row reads), keeps a per-column minimum in registers and
+// folds it into minin with one atomicMin per column.  minin starts at INF.
+constexpr int kColRows = 256;
+__global__ void k_colmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n, int32_t* __restrict__ minin) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kColRows;
+  if (v >= n) return;
+  uint32_t mn = kInf;
+  const int64_t r1 = min(static_cast<int64_t>(n), r0 + kColRows);
+  for (int64_t u = r0; u < r1; ++u) {
+    const uint32_t x = static_cast<uint32_t>(W[u * pitch + v]);
+    if (u != v) mn = min(mn, x);
+  }
+  if (mn < kInf) atomicMin(minin + v, static_cast<int32_t>(mn));
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t value) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = value;
+}
+
 // Columns [n, pitch) of every row hold INF.
 __global__ void k_pad_cols(int32_t* __restrict__ W, int64_t pitch, int32_t n) {
   const int64_t padw = pitch - n;
@@ -128,26 +152,39 @@ static int alloc_graph(int32_t n, int directed, dj_graph** out) {
     delete g;
     return set_error(DJ_ENOMEM, "cudaMalloc of the adjacency matrix failed (" + std::to_string(mbytes) + " bytes)");
   }
-  e = cudaMalloc(&g->minout, static_cast<size_t>(n) * sizeof(int32_t));
+  e = cudaMalloc(&g->minout, 2 * static_cast<size_t>(n) * sizeof(int32_t));
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(g->W);
     delete g;
-    return set_error(DJ_ENOMEM, "cudaMalloc of the row minima failed");
+    return set_error(DJ_ENOMEM, "cudaMalloc of the row / column minima failed");
   }
-  g->bytes = mbytes + static_cast<size_t>(n) * sizeof(int32_t);
+  g->minin = g->minout + n;
+  g->bytes = mbytes + 2 * static_cast<size_t>(n) * sizeof(int32_t);
   *out = g;
   return DJ_OK;
 }
 
-// Row minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
+// Column minima: a copy of the row minima for undirected graphs, else k_colmin.
+static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
+  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
+  if (!g->directed) {
+    cudaMemcpyAsync(g->minin, g->minout, static_cast<size_t>(g->n) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    return;
+  }
+  k_fill_i32<<<grid_for(g->n), 256, 0, st>>>(g->minin, g->n, static_cast<int32_t>(kInf));
+  dim3 grid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
+  k_colmin<<<grid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin);
+}
+
+// Row and column minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
 static int finish_graph(dj_graph* g, cudaStream_t st) {
   uint32_t* stats = nullptr;
   cudaError_t e = cudaMallocAsync(&stats, 2 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(stats)");
   uint32_t init[2] = {kInf, 0};
   cudaMemcpyAsync(stats, init, sizeof(init), cudaMemcpyHostToDevice, st);
-  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
+  launch_minima(g, stats, st);
   uint32_t res[2];
   cudaMemcpyAsync(res, stats, sizeof(res), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(stats, st);
@@ -279,7 +316,7 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
                                     static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
                                     static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(upload)");
-  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, nullptr);
+  launch_minima(g, nullptr, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "row minima");
   return DJ_OK;
@@ -309,6 +346,7 @@ extern "C" int dj_graph_get_info(const dj_graph* g, dj_graph_info* info) {
   info->device = g->device;
   info->matrix = g->W;
   info->minout = g->minout;
+  info->minin = g->minin;
   info->bytes = g->bytes;
   return DJ_OK;
 }
@@ -317,7 +355,7 @@ extern "C" int dj_graph_free(dj_graph* g) {
   clear_error();
   if (!g) return DJ_OK;
   cudaFree(g->W);
-  cudaFree(g->minout);
+  cudaFree(g->minout);  // minin shares this allocation
   delete g;
   return DJ_OK;
 }

@@ -36,7 +36,7 @@ struct GridParams {
   int32_t* pred_out;
   uint32_t* ctl;  // [0] barrier arrivals, [1..3] candidate counters, [5] abort flag
   uint4* partials;  // [2][G]: (key lo, key hi, L_c, count)
-  uint2* cand;      // [2][cand_cap]
+  uint4* cand;      // [2][cand_cap] candidates (u, dist[u], IN key, 0)
   uint32_t* words;  // per-device words: [0] error bits, [1] phases
   int64_t pitch;
   int64_t timeout_ns;
@@ -44,28 +44,33 @@ struct GridParams {
   int32_t nvec_total;
   int32_t source;
   int32_t plain;
+  int32_t use_in;
   uint32_t bits_u;
   uint32_t span;
   uint32_t cand_cap;
   int32_t swcap;
   int32_t rgs_cap;
   int32_t skip_cta;
-  int32_t list_cap;  // staged settled rows per segment
   int32_t depth;     // ring stages per warp
+  int32_t srows;     // rows per ring stage
   int32_t rowcap;    // bytes of one ring row slot
   int32_t trace_cap;
   uint64_t* trace;   // optional per-phase timeline (CTA 0)
 };
 
-// Grid-wide barrier on a monotonic arrival counter (zeroed before launch).
+// Grid-wide barrier on a monotonic arrival counter (zeroed before launch):
+// arrival is a release reduction, waiting an acquire load, so no separate
+// fences are needed.
 // Bounded: after timeout_ns it records kErrTimeout, raises the launch's abort
 // flag and returns false; CTAs already waiting see the flag and leave too.
 __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uint32_t* abort_flag, uint32_t* err,
-                                             int64_t timeout_ns, uint32_t* s_flag) {
+                                             int64_t timeout_ns, uint32_t* s_flag, uint64_t* stamps = nullptr) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    // release: every write of this CTA ordered before the bar.sync above is
+    // visible to a CTA whose acquire load observes the arrival
     red_add_release_gpu(bar, 1u);
+    if (stamps) stamps[0] = global_ns();
     uint32_t ok = 1;
     if (static_cast<int32_t>(ld_acquire_gpu(bar) - target) < 0) {
       const uint64_t t0 = global_ns();
@@ -85,12 +90,25 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uin
         }
       }
     }
-    __threadfence();
     if (ok && ld_relaxed_gpu(abort_flag)) ok = 0;
+    if (stamps) stamps[1] = global_ns();
     *s_flag = ok;
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
+
+// Region of CTA c's published candidates for a phase parity.
+__device__ __forceinline__ int region_of(const uint32_t* off, int nreg, int i) {
+  int lo = 0, hi = nreg;  // off[lo] <= i < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (static_cast<int>(off[mid]) <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
 template <int V, int U, int THREADS>
@@ -98,7 +116,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BlockScratch sc;
   __shared__ Decision s_dec;
-  __shared__ uint32_t s_word;
   __shared__ uint32_t s_flag;
 
   const int G = gridDim.x, b = blockIdx.x;
@@ -108,120 +125,136 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   s.c0 = 4 * v0;
   s.nvec = v1 - v0;
   s.sw = 4 * s.nvec;
+  const int nwarps = static_cast<int>(blockDim.x >> 5);
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
   q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
-  uint2* own = reinterpret_cast<uint2*>(q);
-  q += static_cast<size_t>(p.swcap) * 8;
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(q);  // [G + 1] prefix of the CTAs' candidate counts
+  q += (static_cast<size_t>(G) + 1 + 3) / 4 * 16;
   s.dist = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.pred = reinterpret_cast<int32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
+  s.pdist = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
   s.minout = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.minin = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
   q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
-  uint32_t* list = reinterpret_cast<uint32_t*>(q);
-  q += static_cast<size_t>(p.list_cap) * 4;
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* rings = q;
-  q += static_cast<size_t>(blockDim.x >> 5) * p.depth * U * p.rowcap;
+  q += static_cast<size_t>(nwarps) * p.depth * p.srows * p.rowcap;
   uint64_t* bars = reinterpret_cast<uint64_t*>(q);
+  q += static_cast<size_t>(nwarps) * p.depth * 8;
+  uint32_t* slot_rows = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth;
+  q += static_cast<size_t>(nwarps) * p.depth * 4;
+  uint32_t* slot_tb = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth * U;
 
-  slice_init(s, p.n, p.source, p.minout, !p.plain);
+  slice_init(s, p.n, p.source, p.minout, p.minout + p.n, !p.plain, p.use_in && !p.plain);
   const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
   Ring ring;
-  ring.buf = rings + static_cast<size_t>(warp) * p.depth * U * p.rowcap;
+  ring.buf = rings + static_cast<size_t>(warp) * p.depth * p.srows * p.rowcap;
+  ring.srows = static_cast<uint32_t>(p.srows);
   ring.bar = bars + static_cast<size_t>(warp) * p.depth;
-  ring.lg = static_cast<uint32_t>(__ffs(p.depth) - 1);
+  ring.depth = static_cast<uint32_t>(p.depth);
   ring.gt = 0;
   ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
   if (lane == 0)
     for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
+  if (threadIdx.x == 0) sc.cnt[32] = 0;
   fence_mbar_init();
   __syncthreads();
 
   uint32_t* bar = p.ctl;
-  uint32_t* cnt = p.ctl + 1;
   uint32_t* abort_flag = p.ctl + 5;
+  uint64_t key_t;
+  uint32_t lc_t;
+  slice_partial(s, key_t, lc_t);
   uint32_t phase = 0;
   for (;;) {
-    // 1. publish this slice's partial and candidates
+    // per-phase timeline of CTA 0 (profiling only): 8 stamps per phase
+    uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap) ? p.trace + 8 * phase
+                                                                                           : nullptr;
+    if (tr && threadIdx.x == 0) tr[0] = global_ns();
+    // 1. publish this slice's partial and its candidates (into its own region)
+    uint4* out = p.cand + (static_cast<size_t>(phase & 1) * G + b) * p.swcap;
     uint64_t key;
     uint32_t Lc;
-    const int c = slice_publish(s, p.span, p.plain != 0, own, &key, &Lc, &sc);
-    if (threadIdx.x == 0) {
-      s_word = (c && !p.plain) ? atomicAdd(&cnt[phase % 3], static_cast<uint32_t>(c)) : 0u;
+    const int c = publish_partial(s, p.span, p.plain != 0, p.use_in != 0, key_t, lc_t, out, &sc, &key, &Lc);
+    if (threadIdx.x == 0)
       p.partials[static_cast<size_t>(phase & 1) * G + b] =
           make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
-    }
-    __syncthreads();
-    if (!p.plain) {
-      uint2* dst = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap + s_word;
-      for (int i = threadIdx.x; i < c; i += blockDim.x) dst[i] = own[i];
-    }
     // 2. one grid barrier per phase
+    if (tr && threadIdx.x == 0) tr[1] = global_ns();
     if (b == p.skip_cta) return;  // testing: this CTA never arrives
-    if (!grid_barrier(bar, (phase + 1) * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag))
+    if (!grid_barrier(bar, (phase + 1) * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag,
+                      tr ? tr + 2 : nullptr))
       return;
-    // 3. global decision from the G partials
-    if (threadIdx.x < 32) {
+    // 3. global decision and the prefix of candidate counts, from the G partials
+    if (warp == 0) {
+      const int per = (G + 31) / 32;  // <= kMaxPartialsPerLane (G <= 320)
+      const int i0 = min(G, lane * per), i1 = min(G, i0 + per);
       uint64_t k = kNoKey;
-      uint32_t l = 0xFFFFFFFFu;
+      uint32_t l = 0xFFFFFFFFu, sum = 0;
       const uint4* part = p.partials + static_cast<size_t>(phase & 1) * G;
-      for (int i = threadIdx.x; i < G; i += 32) {
-        const uint4 x = __ldcg(part + i);
+      uint4 xs[kMaxPartialsPerLane];
+#pragma unroll
+      for (int r = 0; r < kMaxPartialsPerLane; ++r)  // all loads in flight at once
+        xs[r] = (i0 + r < i1) ? __ldcg(part + i0 + r) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
+#pragma unroll
+      for (int r = 0; r < kMaxPartialsPerLane; ++r) {
+        const uint4 x = xs[r];
         const uint64_t kk = (static_cast<uint64_t>(x.y) << 32) | x.x;
         k = kk < k ? kk : k;
         l = min(l, x.z);
+        if (i0 + r < i1) s_off[i0 + r] = sum;
+        sum += x.w;
       }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += tt;
+      }
+      for (int i = i0; i < i1; ++i) s_off[i] += incl - sum;
+      if (lane == 31) s_off[G] = incl;
       k = warp_min_u64(k);
       l = warp_min_u32(l);
-      if (threadIdx.x == 0) {
-        s_dec = make_decision(k, l, p.span, p.plain != 0);
-        s_word = p.plain ? 1u : __ldcg(&cnt[phase % 3]);
-        if (b == 0) cnt[(phase + 2) % 3] = 0;  // slot of phase+2's publication, last read in phase-1
+      if (lane == 0) {
+        s_dec = make_decision(k, l, p.span, p.plain != 0, p.use_in != 0);
+        sc.cnt[32] = 0;  // next publication's counter (every thread has read this one)
       }
     }
     __syncthreads();
     const Decision D = s_dec;
-    const int total = static_cast<int>(s_word);
-    const bool tr = p.trace && b == 0 && threadIdx.x == 0 && static_cast<int>(4 * phase + 3) < p.trace_cap;
-    if (tr) p.trace[4 * phase] = global_ns();
-    if (D.m >= kInf) break;
-    slice_mark(s, D);
-    int staged = 0;
-    uint64_t t_staged = 0;
-    // 4. stage the settled rows, then stream their slices through the warps' rings
-    Best<V> best;
-    best_init<V>(best, s, t);
-    bool ok = true;
-    if (p.plain) {
-      if (threadIdx.x == 0) list[0] = D.a;  // its tie-break word: (m - m) << bits | a
-      __syncthreads();
-      ok = relax_list<V, U>(list, 1, s, t, p.W, p.pitch, D.m, p.bits_u, ring, p.timeout_ns, best);
-    } else {
-      const uint2* cl = p.cand + static_cast<size_t>(phase & 1) * p.cand_cap;
-      for (int seg = 0; seg < total; seg += p.list_cap) {
-        const int cnt = stage_list([cl](int i) { return __ldcg(cl + i); }, seg, min(total, seg + p.list_cap), D,
-                                   p.bits_u, list, 0, &sc);
-        staged += cnt;
-        if (tr && seg == 0) t_staged = global_ns();
-        ok = relax_list<V, U>(list, cnt, s, t, p.W, p.pitch, D.m, p.bits_u, ring, p.timeout_ns, best) && ok;
-        __syncthreads();  // the list is rewritten by the next segment
-      }
+    const int total = static_cast<int>(s_off[G]);
+    if (tr && threadIdx.x == 0) {
+      tr[4] = global_ns();
+      tr[7] = static_cast<uint64_t>(total);
     }
+    if (D.m >= kInf) break;
+    // 4. stream the settled rows through the warps' rings and relax this slice
+    Best<V> best;
+    best_init<V>(best, s, t, D, p.bits_u);
+    const uint4* cl = p.cand + static_cast<size_t>(phase & 1) * G * p.swcap;
+    const int swcap = p.swcap;
+    const bool ok = relax_pull<V, U>(
+        [cl, swcap, G, s_off](int i) {
+          const int r = region_of(s_off, G, i);
+          return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
+        },
+        total, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
     if (!ok) {
       atomicOr(p.words, kErrTimeout);
       atomicExch(abort_flag, 1u);
     }
-    if (tr) {
-      p.trace[4 * phase + 1] = t_staged;
-      p.trace[4 * phase + 2] = global_ns();
-      p.trace[4 * phase + 3] = static_cast<uint64_t>(p.plain ? 1 : staged);
-    }
-    merge_commit<V>(s, t, merge, p.bits_u, best);
+    if (tr && threadIdx.x == 0) tr[5] = global_ns();
+    // 5. merge, mark, commit, and the next partial
+    commit_partial<V>(s, t, D, merge, p.bits_u, best, key_t, lc_t);
+    if (tr && threadIdx.x == 0) tr[6] = global_ns();
     ++phase;
   }
   slice_write_out(s, p.n, p.dist_out, p.pred_out);
@@ -296,8 +329,8 @@ struct ClusterParams {
   int64_t timeout_ns;
   int32_t swcap;
   int32_t rgs_cap;
-  int32_t list_cap;
   int32_t depth;
+  int32_t srows;
   int32_t rowcap;
 };
 
@@ -313,31 +346,39 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   __shared__ uint32_t s_addr[16];  // DSMEM address of each rank's candidate list
 
   const uint32_t rank = cluster_rank(), C = cluster_size();
+  const int nwarps = static_cast<int>(blockDim.x >> 5);
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
   q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
-  uint2* own = reinterpret_cast<uint2*>(q);  // [2][swcap]
-  q += static_cast<size_t>(p.swcap) * 16;
+  uint4* own = reinterpret_cast<uint4*>(q);  // [2][swcap], read by the other CTAs of the cluster
+  q += static_cast<size_t>(p.swcap) * 32;
   Slice s;
   s.dist = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.pred = reinterpret_cast<int32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
+  s.pdist = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
   s.minout = reinterpret_cast<uint32_t*>(q);
+  q += static_cast<size_t>(p.swcap) * 4;
+  s.minin = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
   q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
-  uint32_t* list = reinterpret_cast<uint32_t*>(q);
-  q += static_cast<size_t>(p.list_cap) * 4;
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* rings = q;
-  q += static_cast<size_t>(blockDim.x >> 5) * p.depth * U * p.rowcap;
+  q += static_cast<size_t>(nwarps) * p.depth * p.srows * p.rowcap;
   uint64_t* bars = reinterpret_cast<uint64_t*>(q);
+  q += static_cast<size_t>(nwarps) * p.depth * 8;
+  uint32_t* slot_rows = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth;
+  q += static_cast<size_t>(nwarps) * p.depth * 4;
+  uint32_t* slot_tb = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth * U;
   Ring ring;
-  ring.buf = rings + static_cast<size_t>(warp) * p.depth * U * p.rowcap;
+  ring.buf = rings + static_cast<size_t>(warp) * p.depth * p.srows * p.rowcap;
+  ring.srows = static_cast<uint32_t>(p.srows);
   ring.bar = bars + static_cast<size_t>(warp) * p.depth;
-  ring.lg = static_cast<uint32_t>(__ffs(p.depth) - 1);
+  ring.depth = static_cast<uint32_t>(p.depth);
   ring.gt = 0;
   if (lane == 0)
     for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
@@ -345,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   __syncthreads();
 
   for (;;) {
-    // next solve: rank 0 takes it from the queue, every CTA reads it through DSMEM
+    // next solve: rank 0 takes it from the job source, every CTA reads it through DSMEM
     if (rank == 0 && threadIdx.x == 0) {
       uint32_t j = 0;
       s_job = jobs.fetch(&j) ? j : 0xFFFFFFFFu;
@@ -365,68 +406,64 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     s.c0 = 4 * v0;
     s.nvec = v1 - v0;
     s.sw = 4 * s.nvec;
-    slice_init(s, d.n, d.source, d.minout, !d.plain);
+    slice_init(s, d.n, d.source, d.minout, d.minout + d.n, !d.plain, d.use_in && !d.plain);
     const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
     ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
+    if (threadIdx.x == 0) sc.cnt[32] = 0;
     __syncthreads();
 
+    uint64_t key_t;
+    uint32_t lc_t;
+    slice_partial(s, key_t, lc_t);
     uint32_t phase = 0;
     for (;;) {
-      uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
+      uint4* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
       uint64_t key;
       uint32_t Lc;
-      const int c = slice_publish(s, d.span, d.plain != 0, mine, &key, &Lc, &sc);
+      const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, key_t, lc_t, mine, &sc, &key, &Lc);
       if (threadIdx.x == 0)
         s_part[phase & 1] =
             make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
       cluster_sync_all();
-      if (threadIdx.x < 32) {
-        const uint32_t lane = threadIdx.x;
+      if (warp == 0) {
         uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
-        if (lane < C) x = ld_dsmem_u32x4(dsmem_addr(&s_part[phase & 1], lane));
+        if (static_cast<uint32_t>(lane) < C) x = ld_dsmem_u32x4(dsmem_addr(&s_part[phase & 1], lane));
         uint64_t k = (static_cast<uint64_t>(x.y) << 32) | x.x;
         uint32_t l = x.z;
         k = warp_min_u64(k);
         l = warp_min_u32(l);
-        const Decision D = make_decision(k, l, d.span, d.plain != 0);
-        // in plain mode only the argmin row is relaxed: keep the argmin owner's list
         const uint32_t cntv = x.w;
         uint32_t incl = cntv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= static_cast<uint32_t>(o)) incl += tt;
+          if (lane >= o) incl += tt;
         }
-        if (lane < C) {
+        if (static_cast<uint32_t>(lane) < C) {
           s_off[lane] = incl - cntv;
           s_addr[lane] = dsmem_addr(own + static_cast<size_t>(phase & 1) * p.swcap, lane);
         }
-        if (lane == C - 1) s_off[C] = incl;
-        if (lane == 0) s_dec = D;
+        if (static_cast<uint32_t>(lane) == C - 1) s_off[C] = incl;
+        if (lane == 0) {
+          s_dec = make_decision(k, l, d.span, d.plain != 0, d.use_in != 0);
+          sc.cnt[32] = 0;
+        }
       }
       __syncthreads();
       const Decision D = s_dec;
       if (D.m >= kInf) break;
-      slice_mark(s, D);
       Best<V> best;
-      best_init<V>(best, s, t);
+      best_init<V>(best, s, t, D, d.bits_u);
       const int total = static_cast<int>(s_off[C]);
       const int Cn = static_cast<int>(C);
-      auto get = [Cn](int i) {
-        int r = 0;
-#pragma unroll
-        for (int st = 8; st >= 1; st >>= 1)
-          if (r + st < Cn && static_cast<int>(s_off[r + st]) <= i) r += st;
-        return ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
-      };
-      bool ok = true;
-      for (int seg = 0; seg < total; seg += p.list_cap) {
-        const int cnt = stage_list(get, seg, min(total, seg + p.list_cap), D, d.bits_u, list, 0, &sc);
-        ok = relax_list<V, U>(list, cnt, s, t, d.W, d.pitch, D.m, d.bits_u, ring, p.timeout_ns, best) && ok;
-        __syncthreads();
-      }
+      const bool ok = relax_pull<V, U>(
+          [Cn](int i) {
+            const int r = region_of(s_off, Cn, i);
+            return ld_dsmem_u32x4(s_addr[r] + 16u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
+          },
+          total, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
       if (!ok) atomicOr(p.words, kErrTimeout);
-      merge_commit<V>(s, t, merge, d.bits_u, best);
+      commit_partial<V>(s, t, D, merge, d.bits_u, best, key_t, lc_t);
       ++phase;
     }
     slice_write_out(s, d.n, d.dist, d.pred);
@@ -451,21 +488,24 @@ struct Layout {
   int V = 0;
   int swcap = 0;    // columns of the widest slice
   int rgs_cap = 0;  // row groups (merge buffer rows)
-  int list_cap = 0; // staged settled rows per segment
   int depth = 0;    // ring stages per warp
+  int srows = 0;    // rows per stage (<= kRowsPerStage)
   int rowcap = 0;   // bytes of one ring row slot
   size_t smem = 0;
 };
 
-size_t layout_bytes(const Layout& L, int nwarps, int own_copies) {
-  size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (unused with one row group)
-  b += static_cast<size_t>(L.swcap) * 8 * own_copies;        // published candidates
-  b += static_cast<size_t>(L.swcap) * 12;                     // dist, pred, minout
-  b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;         // visited
-  b += static_cast<size_t>(L.list_cap) * 4;                   // staged rows
-  b += 128;                                                   // ring alignment
-  b += static_cast<size_t>(nwarps) * L.depth * kRowsPerStage * L.rowcap;
-  b += static_cast<size_t>(nwarps) * L.depth * 8;             // mbarriers
+// own_copies: published candidate lists kept in shared memory (cluster: 2);
+// offs: prefix entries of the grid engine's candidate counts (grid: G + 1).
+size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
+  size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (one row group: unused)
+  b += static_cast<size_t>(L.swcap) * 16 * own_copies;                           // published candidates
+  b += (static_cast<size_t>(offs) + 3) / 4 * 16;                                 // candidate-count prefix
+  b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
+  b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
+  b += 128;                                                                      // ring alignment
+  b += static_cast<size_t>(nwarps) * L.depth * L.srows * L.rowcap;               // TMA rings
+  b += static_cast<size_t>(nwarps) * L.depth * 8;                                // mbarriers
+  b += static_cast<size_t>(nwarps) * L.depth * (kRowsPerStage + 1) * 4;          // stage row counts + keys
   return b;
 }
 
@@ -476,22 +516,19 @@ int pick_v(int nvec_cta, int nwarps) {
   return 0;
 }
 
-// Fit the layout into `budget` bytes: ring depth first (down to 1), then the list.
-int make_layout(int nvec_cta, int nwarps, int own_copies, int want_depth, int want_list, size_t budget, Layout* L) {
+// Fit the layout into `budget` bytes: the deepest ring up to want_depth stages.
+int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_depth, size_t budget, Layout* L) {
   L->V = pick_v(nvec_cta, nwarps);
   if (!L->V) return set_error(DJ_EUNSUPPORTED, "graph too large for this engine configuration");
   L->swcap = 4 * std::max(nvec_cta, 1);
   const int wpr = std::max(1, (nvec_cta + 32 * L->V - 1) / (32 * L->V));
   L->rgs_cap = std::max(1, nwarps / wpr);
   L->rowcap = std::min(32 * L->V, std::max(nvec_cta, 1)) * 16;
-  want_list = std::max(want_list, 32);
-  for (int depth = want_depth; depth >= 1; depth /= 2) {
-    // keep segments long (>= 512 rows) while ring depth can still give way
-    const int min_list = depth > 1 ? std::min(512, want_list) : 32;
-    for (int list = want_list; list >= min_list; list /= 2) {
+  for (int depth = want_depth; depth >= 1; --depth) {
+    for (int srows = kRowsPerStage; srows >= (depth > 1 ? kRowsPerStage : 1); srows /= 2) {
       L->depth = depth;
-      L->list_cap = list;
-      L->smem = layout_bytes(*L, nwarps, own_copies);
+      L->srows = srows;
+      L->smem = layout_bytes(*L, nwarps, own_copies, offs);
       if (L->smem <= budget) return DJ_OK;
     }
   }
@@ -523,11 +560,6 @@ void* cluster_kernel_for(int v, bool serve = false) {
   return nullptr;
 }
 
-int round_pow2_down(int x) {
-  int p = 1;
-  while (p * 2 <= x) p *= 2;
-  return p;
-}
 
 }  // namespace
 
@@ -538,13 +570,13 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   if (!ctx->coop) return set_error(DJ_EUNSUPPORTED, "device lacks cooperative launch");
   const int nvec_total = g->pitch / 4;
   const int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
-  int G = std::min(ctx->num_sms * per_sm, nvec_total);
+  int G = std::min({ctx->num_sms * per_sm, nvec_total, 32 * kMaxPartialsPerLane});
   const int nwarps = kGridThreads / 32;
   const int nvec_cta = (nvec_total + G - 1) / G;
-  const int want_depth = o.unroll > 0 ? round_pow2_down(std::min(o.unroll, 16)) : 2;
+  const int want_depth = o.unroll > 0 ? std::min(o.unroll, 8) : 2;
   const size_t budget = static_cast<size_t>(ctx->max_smem_optin) / per_sm - 1024;
   Layout L;
-  if (int rc = make_layout(nvec_cta, nwarps, 1, want_depth, g->pitch, budget, &L)) return rc;
+  if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
   void* fn = grid_kernel_for(L.V);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
@@ -556,8 +588,8 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
 
   const size_t ctl_bytes = 256;
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
-  const uint32_t cand_cap = static_cast<uint32_t>(g->pitch);
-  const size_t cand_bytes = static_cast<size_t>(2) * cand_cap * sizeof(uint2);
+  const uint32_t cand_cap = static_cast<uint32_t>(G) * static_cast<uint32_t>(L.swcap);  // one region per CTA
+  const size_t cand_bytes = static_cast<size_t>(2) * cand_cap * sizeof(uint4);
   uint8_t* ws = nullptr;
   e = cudaMallocAsync(&ws, ctl_bytes + part_bytes + cand_bytes, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(grid workspace)");
@@ -570,7 +602,7 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.pred_out = pred;
   p.ctl = reinterpret_cast<uint32_t*>(ws);
   p.partials = reinterpret_cast<uint4*>(ws + ctl_bytes);
-  p.cand = reinterpret_cast<uint2*>(ws + ctl_bytes + part_bytes);
+  p.cand = reinterpret_cast<uint4*>(ws + ctl_bytes + part_bytes);
   p.words = ctx->words;
   p.pitch = g->pitch;
   p.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
@@ -578,14 +610,15 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.nvec_total = nvec_total;
   p.source = source;
   p.plain = o.mode == DJ_MODE_PLAIN ? 1 : 0;
+  p.use_in = (g->wmin >= 1 && o.settle != DJ_SETTLE_OUT) ? 1 : 0;
   p.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
   p.span = host_span_for(static_cast<uint32_t>(g->n));
   p.cand_cap = cand_cap;
   p.swcap = L.swcap;
   p.rgs_cap = L.rgs_cap;
   p.skip_cta = o.debug_skip_cta;
-  p.list_cap = L.list_cap;
   p.depth = L.depth;
+  p.srows = L.srows;
   p.rowcap = L.rowcap;
   p.trace_cap = o.trace ? o.trace_cap : 0;
   p.trace = o.trace;
@@ -605,10 +638,9 @@ static int cluster_layout(int32_t max_pitch, const ClusterLaunch& cl, Layout* L)
   const int nwarps = kClusterThreads / 32;
   // two CTAs per SM when they fit, so clusters of different solves share SMs
   const size_t half = static_cast<size_t>(ctx->max_smem_optin) / 2 - 1024;
-  const int want_list = std::min(max_pitch, 8192);
-  if (make_layout(nvec_cta, nwarps, 2, 2, want_list, half, L) == DJ_OK) return DJ_OK;
+  if (make_layout(nvec_cta, nwarps, 2, 0, 2, half, L) == DJ_OK) return DJ_OK;
   clear_error();
-  return make_layout(nvec_cta, nwarps, 2, 2, want_list, static_cast<size_t>(ctx->max_smem_optin) - 1024, L);
+  return make_layout(nvec_cta, nwarps, 2, 0, 2, static_cast<size_t>(ctx->max_smem_optin) - 1024, L);
 }
 
 static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
@@ -673,8 +705,8 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   plan->smem = L.smem;
   plan->swcap = L.swcap;
   plan->rgs_cap = L.rgs_cap;
-  plan->list_cap = L.list_cap;
   plan->depth = L.depth;
+  plan->srows = L.srows;
   plan->rowcap = L.rowcap;
   plan->words = ctx->words;
   return DJ_OK;
@@ -704,8 +736,8 @@ static ClusterParams params_of(const ClusterPlan& plan) {
   p.timeout_ns = 2000000000LL;
   p.swcap = plan.swcap;
   p.rgs_cap = plan.rgs_cap;
-  p.list_cap = plan.list_cap;
   p.depth = plan.depth;
+  p.srows = plan.srows;
   p.rowcap = plan.rowcap;
   return p;
 }
@@ -755,7 +787,7 @@ SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* p
   d.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
   d.span = host_span_for(static_cast<uint32_t>(g->n));
   d.plain = plain;
-  d.pad = 0;
+  d.use_in = g->wmin >= 1 ? 1 : 0;
   return d;
 }
 
@@ -831,14 +863,14 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   const int nvec_total = g->pitch / 4;
-  const int G = std::min(dv->num_sms, nvec_total);
+  const int G = std::min({dv->num_sms, nvec_total, 32 * kMaxPartialsPerLane});
   const int nwarps = kGridThreads / 32;
   const int nvec_cta = (nvec_total + G - 1) / G;
   Layout L;
-  if (int rc = make_layout(nvec_cta, nwarps, 1, 2, g->pitch, static_cast<size_t>(dv->max_smem_optin) - 1024, &L))
+  if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, 2, static_cast<size_t>(dv->max_smem_optin) - 1024, &L))
     return rc;
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
-  const size_t cand_bytes = static_cast<size_t>(2) * g->pitch * sizeof(uint2);
+  const size_t cand_bytes = static_cast<size_t>(2) * G * L.swcap * sizeof(uint4);
   const size_t need = kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes + cand_bytes;
   if (need > kNoAllocScratchBytes)
     return set_error(DJ_EINVAL, "graph too large for dj_sssp_noalloc: it needs " + std::to_string(need) +
@@ -863,21 +895,22 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.ctl = reinterpret_cast<uint32_t*>(ws);
   p.words = reinterpret_cast<uint32_t*>(ws + kNoAllocCtlBytes);
   p.partials = reinterpret_cast<uint4*>(ws + kNoAllocCtlBytes + kNoAllocWordBytes);
-  p.cand = reinterpret_cast<uint2*>(ws + kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes);
+  p.cand = reinterpret_cast<uint4*>(ws + kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes);
   p.pitch = g->pitch;
   p.timeout_ns = 2000000000LL;
   p.n = g->n;
   p.nvec_total = nvec_total;
   p.source = source;
   p.plain = 0;
+  p.use_in = g->wmin >= 1 ? 1 : 0;
   p.bits_u = host_bits_for(static_cast<uint32_t>(g->n));
   p.span = host_span_for(static_cast<uint32_t>(g->n));
-  p.cand_cap = static_cast<uint32_t>(g->pitch);
+  p.cand_cap = static_cast<uint32_t>(G * L.swcap);
   p.swcap = L.swcap;
   p.rgs_cap = L.rgs_cap;
   p.skip_cta = -1;
-  p.list_cap = L.list_cap;
   p.depth = L.depth;
+  p.srows = L.srows;
   p.rowcap = L.rowcap;
   p.trace_cap = 0;
   p.trace = nullptr;

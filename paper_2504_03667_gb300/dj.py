@@ -32,6 +32,7 @@ DJ_INF = 2**31 - 1
 
 DJ_MODE_AUTO, DJ_MODE_PHASE, DJ_MODE_PLAIN = 0, 1, 2
 DJ_ENGINE_AUTO, DJ_ENGINE_GRID, DJ_ENGINE_CLUSTER = 0, 1, 2
+DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN = 0, 1, 2
 
 
 class DjError(RuntimeError):
@@ -43,14 +44,16 @@ class DjError(RuntimeError):
 class dj_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("pitch", ctypes.c_int32), ("directed", ctypes.c_int32),
                 ("min_weight", ctypes.c_int32), ("max_weight", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("matrix", ctypes.c_void_p), ("minout", ctypes.c_void_p), ("bytes", ctypes.c_uint64)]
+                ("matrix", ctypes.c_void_p), ("minout", ctypes.c_void_p), ("minin", ctypes.c_void_p),
+                ("bytes", ctypes.c_uint64)]
 
 
 class dj_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("engine", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("debug_skip_cta", ctypes.c_int32),
-                ("trace_cap", ctypes.c_int32), ("trace", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
+                ("trace_cap", ctypes.c_int32), ("trace", ctypes.c_void_p), ("settle", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class dj_batch_opts(ctypes.Structure):
@@ -269,7 +272,7 @@ def dj_graph_free(g):
 # ---------------------------------------------------------------------- solves
 
 def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, threads=0, ctas_per_sm=0,
-                    unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None) -> dj_solve_opts:
+                    unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None, settle=0) -> dj_solve_opts:
     """trace: optional int64 CUDA tensor receiving the grid engine's per-phase timeline."""
     o = dj_solve_opts()
     load_library().dj_solve_opts_init(ctypes.byref(o))
@@ -277,6 +280,7 @@ def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, th
     o.ctas_per_sm, o.unroll, o.timeout_ns, o.debug_skip_cta = ctas_per_sm, unroll, timeout_ns, debug_skip_cta
     if trace is not None:
         o.trace, o.trace_cap = int(trace.data_ptr()), int(trace.numel())
+    o.settle = settle
     return o
 
 
