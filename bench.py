@@ -364,6 +364,7 @@ def print_trace(dj, torch, g, source: int, n: int, stream):
         rows.append(d_)
     sums = {nm: sum(r[nm] for r in rows) for nm in names}
     print(json.dumps({"phases": phases, "total_us": (t[phases, 4] - t[0, 0]) / 1e3, "sums_us": sums,
+                      "candidates_total": int(sum(r["candidates"] for r in rows)), "n": n,
                       "per_phase": rows if phases <= 64 else rows[:8]}), flush=True)
 
 

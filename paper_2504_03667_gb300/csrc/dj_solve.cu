@@ -241,12 +241,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     best_init<V>(best, s, t, D, p.bits_u);
     const uint4* cl = p.cand + static_cast<size_t>(phase & 1) * G * p.swcap;
     const int swcap = p.swcap;
-    const bool ok = relax_pull<V, U>(
-        [cl, swcap, G, s_off](int i) {
-          const int r = region_of(s_off, G, i);
-          return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
-        },
-        total, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+    bool ok;
+    if (p.plain) {  // Algorithm 1's single row a: no candidate list to read
+      const uint4 one = make_uint4(D.a, D.m, 0u, 0u);
+      ok = relax_pull<V, U>([one](int) { return one; }, 1, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows,
+                            slot_tb, p.timeout_ns, best);
+    } else {
+      ok = relax_pull<V, U>(
+          [cl, swcap, G, s_off](int i) {
+            const int r = region_of(s_off, G, i);
+            return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
+          },
+          total, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+    }
     if (!ok) {
       atomicOr(p.words, kErrTimeout);
       atomicExch(abort_flag, 1u);
@@ -456,12 +463,19 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       best_init<V>(best, s, t, D, d.bits_u);
       const int total = static_cast<int>(s_off[C]);
       const int Cn = static_cast<int>(C);
-      const bool ok = relax_pull<V, U>(
-          [Cn](int i) {
-            const int r = region_of(s_off, Cn, i);
-            return ld_dsmem_u32x4(s_addr[r] + 16u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
-          },
-          total, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+      bool ok;
+      if (d.plain) {  // Algorithm 1's single row a: no candidate list to read
+        const uint4 one = make_uint4(D.a, D.m, 0u, 0u);
+        ok = relax_pull<V, U>([one](int) { return one; }, 1, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows,
+                              slot_tb, p.timeout_ns, best);
+      } else {
+        ok = relax_pull<V, U>(
+            [Cn](int i) {
+              const int r = region_of(s_off, Cn, i);
+              return ld_dsmem_u32x4(s_addr[r] + 16u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
+            },
+            total, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+      }
       if (!ok) atomicOr(p.words, kErrTimeout);
       commit_partial<V>(s, t, D, merge, d.bits_u, best, key_t, lc_t);
       ++phase;
@@ -509,8 +523,12 @@ size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
   return b;
 }
 
-// smallest V in {1, 2, 4} whose column chunks fit the warps (at least one row group)
+// V (vec4 per lane): the smallest that lets one warp cover the whole slice, so
+// every warp is its own row group (most rows in flight); else the smallest
+// whose column chunks fit the warps.
 int pick_v(int nvec_cta, int nwarps) {
+  for (int v : {1, 2, 4})
+    if (nvec_cta <= 32 * v) return v;
   for (int v : {1, 2, 4})
     if ((nvec_cta + 32 * v - 1) / (32 * v) <= nwarps) return v;
   return 0;
