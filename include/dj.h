@@ -211,7 +211,8 @@ typedef struct dj_batch_opts {
   int32_t cluster_size;  /* 0 = auto (autotuned table or heuristic) */
   int32_t threads;       /* 0 = auto */
   int32_t clusters;      /* clusters resident at once, 0 = as many as fit */
-  int32_t reserved[8];
+  int32_t settle;        /* DJ_SETTLE_* (defined below), 0 = auto */
+  int32_t reserved[7];
 } dj_batch_opts;
 
 void dj_batch_opts_init(dj_batch_opts* opts);

@@ -252,6 +252,8 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
   if (int rc = batch_descs(graphs, sources, k, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0, ctx->device, &h, &max_n,
                            &max_pitch))
     return rc;
+  if (o.settle == DJ_SETTLE_OUT)
+    for (auto& d : h) d.use_in = 0;
   auto* b = new dj_batch();
   b->device = ctx->device;
   b->k = k;

@@ -145,11 +145,19 @@ __device__ __forceinline__ void slice_partial(const Slice& s, uint64_t& key, uin
 }
 
 // Step 1: reduce the per-thread partials to the slice's (key, L_c) and append
-// the candidates {unvisited v : dist[v] < L_c} u {argmin} as (v, dist[v]) to
-// `out` (order irrelevant: the relaxation keys are order-free).  sc->cnt[32]
+// the candidates {unvisited v : dist[v] < L_c} u {IN candidates} u {argmin} as
+// (v, dist[v][, IN key]) to `out` (order irrelevant: the relaxation keys are order-free).  sc->cnt[32]
 // must be zero on entry.  Returns the count; all threads get key, Lc, count.
+__device__ __forceinline__ void put_entry(uint4* out, uint32_t v, uint32_t d, uint32_t ik) {
+  *out = make_uint4(v, d, ik, 0u);
+}
+__device__ __forceinline__ void put_entry(uint2* out, uint32_t v, uint32_t d, uint32_t) {
+  *out = make_uint2(v, d);  // readers recompute the IN key from minin
+}
+
+template <class Entry>
 __device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bool plain, bool use_in,
-                                               uint64_t key_t, uint32_t lc_t, uint4* out, BlockScratch* sc,
+                                               uint64_t key_t, uint32_t lc_t, Entry* out, BlockScratch* sc,
                                                uint64_t* key_out, uint32_t* Lc_out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   uint64_t k = warp_min_u64(key_t);
@@ -188,7 +196,7 @@ __device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bo
         uint32_t pos = 0;
         if (lane == 0) pos = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
         pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (p) out[pos + __popc(bal & ((1u << lane) - 1u))] = make_uint4(static_cast<uint32_t>(s.c0 + j), d, ik, 0u);
+        if (p) put_entry(out + pos + __popc(bal & ((1u << lane) - 1u)), static_cast<uint32_t>(s.c0 + j), d, ik);
       }
     }
   }
@@ -318,6 +326,46 @@ __device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key
     s.pred[col] = static_cast<int32_t>(tb & ((1u << bits_u) - 1u));
     s.pdist[col] = D.m + (tb >> bits_u);
   }
+}
+
+// Stage the settled entries among candidates [begin, end) of get(i) into the
+// CTA's own shared-memory list as 32-bit tie words tb = ((dist[u] - m) << bits) | u
+// (order irrelevant), so that warps read them locally afterwards.  All
+// threads take part, K loads each in flight; returns the count; ends synced.
+template <class Get>
+__device__ __forceinline__ int stage_settled(const Get& get, int begin, int end, const Decision& D, uint32_t bits_u,
+                                             uint32_t* list, BlockScratch* sc) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) sc->cnt[31] = 0;
+  __syncthreads();
+  constexpr int K = 4;
+  for (int i0 = begin; i0 < end; i0 += K * blockDim.x) {
+    uint4 e[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = i0 + k * blockDim.x + threadIdx.x;
+      e[k] = i < end ? get(i) : make_uint4(0xffffffffu, kInf, kInf, 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool p = e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, e[k].z, D);
+      const uint32_t bal = __ballot_sync(0xffffffffu, p);
+      if (bal) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(&sc->cnt[31], static_cast<uint32_t>(__popc(bal)));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (p) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((e[k].y - D.m) << bits_u) | e[k].x;
+      }
+    }
+  }
+  __syncthreads();
+  return static_cast<int>(sc->cnt[31]);
+}
+
+// Entry i of a staged list, in the candidate form the relaxation takes.
+__device__ __forceinline__ uint4 staged_entry(const uint32_t* list, int i, const Decision& D, uint32_t bits_u) {
+  const uint32_t tb = list[i];
+  return make_uint4(tb & ((1u << bits_u) - 1u), D.m + (tb >> bits_u), 0u, 0u);
 }
 
 // Relax the settled rows among `total` candidates (u, dist[u], IN key) given by

@@ -90,6 +90,7 @@ struct ClusterPlan {
   int depth = 0;
   int srows = 0;
   int rowcap = 0;
+  int list_cap = 0;
   uint32_t* words = nullptr;
 };
 int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve = false);

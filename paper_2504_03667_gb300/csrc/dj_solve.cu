@@ -339,6 +339,7 @@ struct ClusterParams {
   int32_t depth;
   int32_t srows;
   int32_t rowcap;
+  int32_t list_cap;  // staged settled rows per segment
 };
 
 template <int V, int U, int THREADS, class Jobs>
@@ -357,8 +358,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
   q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
-  uint4* own = reinterpret_cast<uint4*>(q);  // [2][swcap], read by the other CTAs of the cluster
-  q += static_cast<size_t>(p.swcap) * 32;
+  uint2* own = reinterpret_cast<uint2*>(q);  // [2][swcap] (v, dist[v]), read by the other CTAs of the cluster
+  q += static_cast<size_t>(p.swcap) * 16;
   Slice s;
   s.dist = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
@@ -372,6 +373,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
   q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+  uint32_t* list = reinterpret_cast<uint32_t*>(q);  // staged settled rows of the cluster
+  q += static_cast<size_t>(p.list_cap) * 4;
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* rings = q;
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     slice_partial(s, key_t, lc_t);
     uint32_t phase = 0;
     for (;;) {
-      uint4* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
+      uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
       uint64_t key;
       uint32_t Lc;
       const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, key_t, lc_t, mine, &sc, &key, &Lc);
@@ -469,12 +472,24 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
         ok = relax_pull<V, U>([one](int) { return one; }, 1, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows,
                               slot_tb, p.timeout_ns, best);
       } else {
-        ok = relax_pull<V, U>(
-            [Cn](int i) {
-              const int r = region_of(s_off, Cn, i);
-              return ld_dsmem_u32x4(s_addr[r] + 16u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
-            },
-            total, s, t, d.W, d.pitch, D, d.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+        // stage the cluster's settled rows locally (one pass of remote reads by
+        // all threads), then every warp pulls them from its own shared memory
+        ok = true;
+        const uint32_t bu = d.bits_u;
+        for (int seg = 0; seg < total; seg += p.list_cap) {
+          const int32_t* minin_g = d.minout + d.n;
+          const int cnt = stage_settled(
+              [Cn, minin_g](int i) {
+                const int r = region_of(s_off, Cn, i);
+                const uint2 e = ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
+                return make_uint4(e.x, e.y, in_key(e.y, static_cast<uint32_t>(__ldg(minin_g + e.x))), 0u);
+              },
+              seg, min(total, seg + p.list_cap), D, bu, list, &sc);
+          ok = relax_pull<V, U>([list, D, bu](int i) { return staged_entry(list, i, D, bu); }, cnt, s, t, d.W,
+                                d.pitch, D, bu, ring, slot_rows, slot_tb, p.timeout_ns, best) &&
+               ok;
+          __syncthreads();  // the list is rewritten by the next segment
+        }
       }
       if (!ok) atomicOr(p.words, kErrTimeout);
       commit_partial<V>(s, t, D, merge, d.bits_u, best, key_t, lc_t);
@@ -504,6 +519,7 @@ struct Layout {
   int rgs_cap = 0;  // row groups (merge buffer rows)
   int depth = 0;    // ring stages per warp
   int srows = 0;    // rows per stage (<= kRowsPerStage)
+  int list_cap = 0; // cluster engine: staged settled rows per segment
   int rowcap = 0;   // bytes of one ring row slot
   size_t smem = 0;
 };
@@ -511,11 +527,13 @@ struct Layout {
 // own_copies: published candidate lists kept in shared memory (cluster: 2);
 // offs: prefix entries of the grid engine's candidate counts (grid: G + 1).
 size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
+  // L.list_cap: staged settled rows (cluster engine only)
   size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (one row group: unused)
   b += static_cast<size_t>(L.swcap) * 16 * own_copies;                           // published candidates
   b += (static_cast<size_t>(offs) + 3) / 4 * 16;                                 // candidate-count prefix
   b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
   b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
+  b += static_cast<size_t>(L.list_cap) * 4;                                      // staged rows
   b += 128;                                                                      // ring alignment
   b += static_cast<size_t>(nwarps) * L.depth * L.srows * L.rowcap;               // TMA rings
   b += static_cast<size_t>(nwarps) * L.depth * 8;                                // mbarriers
@@ -534,7 +552,8 @@ int pick_v(int nvec_cta, int nwarps) {
   return 0;
 }
 
-// Fit the layout into `budget` bytes: the deepest ring up to want_depth stages.
+// Fit the layout into `budget` bytes: the deepest ring up to want_depth stages,
+// with the longest stages (up to kRowsPerStage rows) that fit at that depth.
 int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_depth, size_t budget, Layout* L) {
   L->V = pick_v(nvec_cta, nwarps);
   if (!L->V) return set_error(DJ_EUNSUPPORTED, "graph too large for this engine configuration");
@@ -543,7 +562,7 @@ int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_dep
   L->rgs_cap = std::max(1, nwarps / wpr);
   L->rowcap = std::min(32 * L->V, std::max(nvec_cta, 1)) * 16;
   for (int depth = want_depth; depth >= 1; --depth) {
-    for (int srows = kRowsPerStage; srows >= (depth > 1 ? kRowsPerStage : 1); srows /= 2) {
+    for (int srows = kRowsPerStage; srows >= 1; srows /= 2) {
       L->depth = depth;
       L->srows = srows;
       L->smem = layout_bytes(*L, nwarps, own_copies, offs);
@@ -656,9 +675,12 @@ static int cluster_layout(int32_t max_pitch, const ClusterLaunch& cl, Layout* L)
   const int nwarps = kClusterThreads / 32;
   // two CTAs per SM when they fit, so clusters of different solves share SMs
   const size_t half = static_cast<size_t>(ctx->max_smem_optin) / 2 - 1024;
-  if (make_layout(nvec_cta, nwarps, 2, 0, 2, half, L) == DJ_OK) return DJ_OK;
+  L->list_cap = std::min(max_pitch, 512);
+  // full 8-row stages first (short stages stream markedly slower); two CTAs per SM if that still fits
+  // two 8-byte candidate lists = one 16-byte "copy" in the layout arithmetic
+  if (make_layout(nvec_cta, nwarps, 1, 0, 2, half, L) == DJ_OK && L->srows == kRowsPerStage) return DJ_OK;
   clear_error();
-  return make_layout(nvec_cta, nwarps, 2, 0, 2, static_cast<size_t>(ctx->max_smem_optin) - 1024, L);
+  return make_layout(nvec_cta, nwarps, 1, 0, 2, static_cast<size_t>(ctx->max_smem_optin) - 1024, L);
 }
 
 static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
@@ -726,6 +748,7 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   plan->depth = L.depth;
   plan->srows = L.srows;
   plan->rowcap = L.rowcap;
+  plan->list_cap = L.list_cap;
   plan->words = ctx->words;
   return DJ_OK;
 }
@@ -757,6 +780,7 @@ static ClusterParams params_of(const ClusterPlan& plan) {
   p.depth = plan.depth;
   p.srows = plan.srows;
   p.rowcap = plan.rowcap;
+  p.list_cap = plan.list_cap;
   return p;
 }
 

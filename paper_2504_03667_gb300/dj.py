@@ -58,7 +58,7 @@ class dj_solve_opts(ctypes.Structure):
 
 class dj_batch_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("clusters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("clusters", ctypes.c_int32), ("settle", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class dj_serve_opts(ctypes.Structure):
@@ -356,10 +356,10 @@ class Batch:
 
 
 def dj_batch_create(graphs: Sequence, sources, dists: Sequence, preds: Sequence, mode=DJ_MODE_AUTO,
-                    cluster_size=0, clusters=0) -> Batch:
+                    cluster_size=0, clusters=0, settle=DJ_SETTLE_AUTO) -> Batch:
     o = dj_batch_opts()
     load_library().dj_batch_opts_init(ctypes.byref(o))
-    o.mode, o.cluster_size, o.clusters = mode, cluster_size, clusters
+    o.mode, o.cluster_size, o.clusters, o.settle = mode, cluster_size, clusters, settle
     k = len(graphs)
     g = _ptr_array([_gh(x) for x in graphs])
     s = _host_i32(sources)
