@@ -318,7 +318,9 @@ def main():
 
 def _traffic(n: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_sssp_grid_dense_n8192_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"k_sssp_grid_dense_n{n}_traffic.txt")
+    if not os.path.exists(path):
+        path = os.path.join(ROOT, "profiles", "k_sssp_grid_dense_n8192_traffic.txt")
     try:
         kv = {}
         for ln in open(path):
@@ -329,6 +331,8 @@ def _traffic(n: int):
             return None, "kernel changed since the ncu capture"
         base_n = int(kv["n"])
         per = int(kv["dram_bytes_per_launch"])
+        if base_n == n:
+            return per, f"ncu dram__bytes_read+write of one launch at n={n} (1-pass capture)"
         return per * (n / base_n) ** 2, f"ncu dram__bytes_read+write at n={base_n}, scaled by n^2"
     except (OSError, KeyError, ValueError):
         return None, "no ncu capture"
@@ -353,17 +357,19 @@ def print_trace(dj, torch, g, source: int, n: int, stream):
     dj.dj_sssp_ex(g, source, d, p, dj.make_solve_opts(engine=dj.DJ_ENGINE_GRID, trace=tr), stream)
     dj.dj_sync(stream)
     phases = dj.dj_last_phases()
-    t = tr.cpu().numpy().reshape(-1, 8)[: phases + 1]
+    tall = tr.cpu().numpy()
+    t = tall.reshape(-1, 8)[: phases + 1]
     names = ["publish_us", "arrive_us", "barrier_wait_us", "decision_us", "relax_us", "commit_us"]
     rows = []
     for i in range(phases):
-        d_ = {"phase": i, "candidates": int(t[i, 7])}
+        d_ = {"phase": i, "candidates": int(t[i, 7]) & 0xFFFFFFFF, "cta0_live_groups": int(t[i, 7]) >> 32}
         for k, nm in enumerate(names):
             d_[nm] = (t[i, k + 1] - t[i, k]) / 1e3
-        d_["relax_gbs_upper"] = int(t[i, 7]) * n * 4 / max(t[i, 5] - t[i, 4], 1)
+        d_["relax_gbs_upper"] = d_["candidates"] * n * 4 / max(t[i, 5] - t[i, 4], 1)
         rows.append(d_)
     sums = {nm: sum(r[nm] for r in rows) for nm in names}
     print(json.dumps({"phases": phases, "total_us": (t[phases, 4] - t[0, 0]) / 1e3, "sums_us": sums,
+                      "prologue_us": (t[0, 0] - tall[-2]) / 1e3, "epilogue_us": (tall[-1] - t[phases, 4]) / 1e3,
                       "candidates_total": int(sum(r["candidates"] for r in rows)), "n": n,
                       "per_phase": rows if phases <= 64 else rows[:8]}), flush=True)
 

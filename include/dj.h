@@ -133,9 +133,17 @@ typedef struct dj_solve_opts {
   uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 records 8 words:
                              %globaltimer at publish start, publish end, barrier arrival, barrier
                              exit, decision end, relaxation end, commit end, then the phase's
-                             candidate count; unused entries are left as is */
+                             candidate count (low 32 bits) and CTA 0's live column groups (high
+                             32 bits); the last two entries get CTA 0's kernel entry and exit
+                             times (trace_cap >= 10); unused entries are left as is */
   int32_t settle;         /* phase mode's settle bounds: DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN */
-  int32_t reserved[1];
+  int32_t live;           /* grid engine column filter.  A settled row u offers column v at least
+                             max(L, m + minin[v]), so a column whose stored dist is below that can
+                             change neither dist nor pred in this phase.  0 = auto: a CTA with no
+                             live column skips the phase's relaxation, one with few live columns
+                             loads only those; > 0: load only the live columns when at most this
+                             many 4-column groups of the CTA's slice are live; -1 = off (every
+                             settled row's whole slice is streamed). */
 } dj_solve_opts;
 
 #define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only */

@@ -36,6 +36,13 @@
 //     key (candidate, dist[u], u) with the stored (dist[v], dist[pred[v]],
 //     pred[v]); the surviving pred is the u of smallest (dist[u], u) offering
 //     dist[v], which is the one Algorithm 1 keeps when weights are >= 1.
+//   - Column filter: every u in S was unvisited when the phase began, so it
+//     offers v at least max(L, m + minin[v]).  Columns whose stored dist is
+//     below that bound cannot change this phase, and one equal to it can only
+//     take a tie, from a row whose tie word is below the column's stored one.
+//     A CTA whose slice has no such "live" column skips the relaxation; one
+//     with few live columns loads only their 16-byte groups, and only from
+//     the rows that can still win there (relax_gather).
 // All sums are unsigned 32-bit: dist <= INF and G <= INF, so dist + G never
 // wraps, and an INF entry yields a candidate >= INF that never improves.
 #pragma once
@@ -328,6 +335,50 @@ __device__ __forceinline__ void commit_key(const Slice& s, int col, uint64_t key
   }
 }
 
+// Whether a row of this phase's settled set S can still change column j.
+// Every u in S was unvisited when the phase began, so it offers v at least
+// max(L, m + minin[v]): L <= dist[u] + minout[u] <= dist[u] + G[u][v], and
+// dist[u] >= m with G[u][v] >= minin[v] (that term only with the IN bound's
+// data loaded).  A column whose stored dist is below the bound keeps both
+// dist and pred this phase; one equal to it can only take a tie, which
+// commits only when its stored pred can be tie-beaten (stored_tie != 0, never
+// without the IN bound).  Padding columns (visited, INF) never take part.
+// Returned as the row threshold of the column: 0 = not live; 2^32 = any
+// settled row may strictly improve it; otherwise only a tie can commit, so
+// only rows whose tie word is below this (stored_tie) matter.
+__device__ __forceinline__ uint64_t column_live(const Slice& s, int j, const Decision& D, uint32_t bits_u) {
+  const uint32_t d = s.dist[j];
+  if (s.vis[j] && d >= kInf) return 0u;
+  uint32_t bound = D.L;
+  if (D.use_in) bound = max(bound, D.m + s.minin[j]);  // m < INF, minin <= INF: no wrap
+  if (d != bound) return d > bound ? (1ull << 32) : 0u;
+  return stored_tie(s, j, D, bits_u);
+}
+
+// The 4-column groups of this slice that hold a live column, into glist (any
+// order), with the group's row threshold (the largest of its columns') in
+// gthr.  Returns their count; ends synced.
+__device__ __forceinline__ int live_groups(const Slice& s, const Decision& D, uint32_t bits_u, uint32_t* glist,
+                                           uint64_t* gthr, BlockScratch* sc) {
+  if (threadIdx.x == 0) sc->cnt[30] = 0;
+  __syncthreads();
+  for (int jv = threadIdx.x; jv < s.nvec; jv += blockDim.x) {
+    uint64_t thr = column_live(s, 4 * jv, D, bits_u);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+      const uint64_t t = column_live(s, 4 * jv + c, D, bits_u);
+      thr = t > thr ? t : thr;
+    }
+    if (thr) {
+      const uint32_t i = atomicAdd(&sc->cnt[30], 1u);
+      glist[i] = static_cast<uint32_t>(jv);
+      gthr[i] = thr;
+    }
+  }
+  __syncthreads();
+  return static_cast<int>(sc->cnt[30]);
+}
+
 // Stage the settled entries among candidates [begin, end) of get(i) into the
 // CTA's own shared-memory list as 32-bit tie words tb = ((dist[u] - m) << bits) | u
 // (order irrelevant), so that warps read them locally afterwards.  All
@@ -338,7 +389,8 @@ __device__ __forceinline__ int stage_settled(const Get& get, int begin, int end,
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) sc->cnt[31] = 0;
   __syncthreads();
-  constexpr int K = 4;
+  constexpr int K = 8;
+  const uint32_t lt = (1u << lane) - 1u;
   for (int i0 = begin; i0 < end; i0 += K * blockDim.x) {
     uint4 e[K];
 #pragma unroll
@@ -346,15 +398,22 @@ __device__ __forceinline__ int stage_settled(const Get& get, int begin, int end,
       const int i = i0 + k * blockDim.x + threadIdx.x;
       e[k] = i < end ? get(i) : make_uint4(0xffffffffu, kInf, kInf, 0u);
     }
+    // one reservation per warp for all K ballots
+    uint32_t bal[K];
+    uint32_t tot = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const bool p = e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, e[k].z, D);
-      const uint32_t bal = __ballot_sync(0xffffffffu, p);
-      if (bal) {
-        uint32_t pos = 0;
-        if (lane == 0) pos = atomicAdd(&sc->cnt[31], static_cast<uint32_t>(__popc(bal)));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (p) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((e[k].y - D.m) << bits_u) | e[k].x;
+      bal[k] = __ballot_sync(0xffffffffu, e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, e[k].z, D));
+      tot += __popc(bal[k]);
+    }
+    if (tot) {
+      uint32_t pos = 0;
+      if (lane == 0) pos = atomicAdd(&sc->cnt[31], tot);
+      pos = __shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if ((bal[k] >> lane) & 1u) list[pos + __popc(bal[k] & lt)] = ((e[k].y - D.m) << bits_u) | e[k].x;
+        pos += __popc(bal[k]);
       }
     }
   }
@@ -484,6 +543,96 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
   return ok;
 }
 
+// Relax only the live groups glist[0, nlg) of this slice: the settled rows
+// among `total` candidates get(i) are staged into `list` (list_cap at a time)
+// and cut into chunks of kGatherChunk rows; work item (chunk c, group g) goes
+// to thread (c * nlg + g) mod blockDim, so a group that needs every row is
+// spread over the whole block.  An item loads the group's 16 bytes of each of
+// its rows whose tie word is below the group's threshold gthr[g] (all of them
+// in flight at once), keeps the running best of the group's 4 columns, and merges it
+// into bkey (64-bit keys (candidate << 32) | tie word, shared-memory
+// atomicMin).  On entry bkey[j] must hold (dist[j] << 32) | ~0 for every
+// column.  Ends synced.
+constexpr int kGatherChunk = 16;
+template <class Get>
+__device__ __forceinline__ void relax_gather(const Get& get, int total, const Slice& s,
+                                             const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
+                                             uint32_t bits_u, const uint32_t* glist, const uint64_t* gthr,
+                                             int nlg, uint32_t* list, int list_cap, uint64_t* bkey,
+                                             BlockScratch* sc) {
+  const uint32_t umask = (1u << bits_u) - 1u;
+  constexpr int K = kGatherChunk;
+  for (int seg = 0; seg < total; seg += list_cap) {
+    const int cnt = stage_settled(get, seg, min(total, seg + list_cap), D, bits_u, list, sc);
+    const int items = nlg * ((cnt + kGatherChunk - 1) / kGatherChunk);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int c = it / nlg, g = it - c * nlg;
+      const uint64_t thr = gthr[g];
+      const int col = 4 * static_cast<int>(glist[g]);
+      const int32_t* base = W + s.c0 + col;
+      uint32_t bc[4], bt[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bc[q] = s.dist[col + q];
+        bt[q] = 0xFFFFFFFFu;
+      }
+      const int r1 = min(cnt, (c + 1) * kGatherChunk);
+      for (int r0 = c * kGatherChunk; r0 < r1; r0 += K) {
+        int4 x[K];
+        uint32_t tbk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int r = r0 + k;
+          tbk[k] = r < r1 ? list[r] : 0u;
+          const bool need = r < r1 && tbk[k] < thr;
+          x[k] = need ? __ldg(reinterpret_cast<const int4*>(base + static_cast<int64_t>(tbk[k] & umask) * pitch))
+                      : make_int4(0, 0, 0, 0);
+          if (!need) tbk[k] = 0xFFFFFFFFu;  // marks the slot unused
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (tbk[k] == 0xFFFFFFFFu) continue;
+          const uint32_t du = D.m + (tbk[k] >> bits_u);
+          best_update(du + static_cast<uint32_t>(x[k].x), tbk[k], bc[0], bt[0]);
+          best_update(du + static_cast<uint32_t>(x[k].y), tbk[k], bc[1], bt[1]);
+          best_update(du + static_cast<uint32_t>(x[k].z), tbk[k], bc[2], bt[2]);
+          best_update(du + static_cast<uint32_t>(x[k].w), tbk[k], bc[3], bt[3]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (bt[q] == 0xFFFFFFFFu) continue;  // nothing offered
+        const uint64_t key = (static_cast<uint64_t>(bc[q]) << 32) | bt[q];
+        unsigned long long* slot = reinterpret_cast<unsigned long long*>(bkey + col + q);
+        if (key < *slot) atomicMin(slot, static_cast<unsigned long long>(key));
+      }
+    }
+    __syncthreads();  // bkey complete; the list is rewritten by the next segment
+  }
+}
+
+// One column of a commit: mark it visited if it was settled this phase
+// (judged on its state before the commit), commit a lexicographically
+// smaller key b, and fold the column into this thread's next partial.
+__device__ __forceinline__ void commit_column(const Slice& s, int col, uint64_t b, const Decision& D,
+                                              uint32_t bits_u, uint64_t& key, uint32_t& lc) {
+  const uint32_t d = s.dist[col];
+  const uint32_t tie0 = stored_tie(s, col, D, bits_u);
+  if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
+  commit_key(s, col, b, tie0, D, bits_u);
+  column_partial(s, col, key, lc);
+}
+
+// Commit from the per-column keys of relax_gather, or from none (bkey null:
+// no live column in the slice).
+__device__ __forceinline__ void commit_keys(const Slice& s, const Decision& D, uint32_t bits_u, const uint64_t* bkey,
+                                            uint64_t& key, uint32_t& lc) {
+  key = kNoKey;
+  lc = 0xFFFFFFFFu;
+  for (int col = threadIdx.x; col < s.sw; col += blockDim.x)
+    commit_column(s, col, bkey ? bkey[col] : kNoKey, D, bits_u, key, lc);
+}
+
 // Merge the row groups' bests, then for every column: mark it visited if it
 // was settled this phase (judged on its state before this phase's commit),
 // commit a lexicographically smaller key, and fold the column into this
@@ -496,13 +645,7 @@ __device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, co
   const int lane = threadIdx.x & 31;
   key = kNoKey;
   lc = 0xFFFFFFFFu;
-  auto one = [&](int col, uint64_t b) {
-    const uint32_t d = s.dist[col];
-    const uint32_t tie0 = stored_tie(s, col, D, bits_u);
-    if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
-    commit_key(s, col, b, tie0, D, bits_u);
-    column_partial(s, col, key, lc);
-  };
+  auto one = [&](int col, uint64_t b) { commit_column(s, col, b, D, bits_u, key, lc); };
   if (t.rgs == 1) {
     if (t.active) {
 #pragma unroll

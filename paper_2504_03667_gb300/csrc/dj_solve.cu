@@ -56,6 +56,8 @@ struct GridParams {
   int32_t rowcap;    // bytes of one ring row slot
   int32_t trace_cap;
   uint64_t* trace;   // optional per-phase timeline (CTA 0)
+  int32_t list_cap;    // staged settled rows per segment (column-filtered relaxation)
+  int32_t gather_max;  // load only the live columns when at most this many groups are live (-1: never filter)
 };
 
 // Grid-wide barrier on a monotonic arrival counter (zeroed before launch):
@@ -100,15 +102,46 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uin
 
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
 
-// Region of CTA c's published candidates for a phase parity.
+// The region (publishing CTA) of entry i of a phase's candidate list: the
+// largest r with off[r] <= i < off[r + 1] (off: prefix of the regions'
+// counts).  Branch-free fixed-depth search (nreg <= 512).
 __device__ __forceinline__ int region_of(const uint32_t* off, int nreg, int i) {
-  int lo = 0, hi = nreg;  // off[lo] <= i < off[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (static_cast<int>(off[mid]) <= i) lo = mid;
-    else hi = mid;
+  int lo = 0;
+#pragma unroll
+  for (int step = 256; step >= 1; step >>= 1) {
+    const int c = lo + step;
+    lo = (c < nreg && static_cast<int>(off[min(c, nreg - 1)]) <= i) ? c : lo;
   }
   return lo;
+}
+
+// region_of for a cluster's lists (nreg <= 16).
+__device__ __forceinline__ int region_of16(const uint32_t* off, int nreg, int i) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 8; step >= 1; step >>= 1) {
+    const int c = lo + step;
+    lo = (c < nreg && static_cast<int>(off[min(c, nreg - 1)]) <= i) ? c : lo;
+  }
+  return lo;
+}
+
+// Chunk table of a candidate list: ctab[c] = region of entry 32 c.  Built by
+// threads r < nreg in parallel from the prefix off; every chunk start lies in
+// exactly one non-empty region.
+__device__ __forceinline__ void build_chunk_table(const uint32_t* off, int nreg, uint32_t* ctab) {
+  for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
+    const uint32_t a = off[r], b = off[r + 1];
+    for (uint32_t c = (a + 31) >> 5; (c << 5) < b; ++c) ctab[c] = static_cast<uint32_t>(r);
+  }
+}
+
+// region_of through the chunk table: a start region, then a walk past region
+// ends (empty regions included) up to entry i.
+__device__ __forceinline__ int region_at(const uint32_t* off, const uint32_t* ctab, int i) {
+  int r = static_cast<int>(ctab[i >> 5]);
+  while (static_cast<int>(off[r + 1]) <= i) ++r;
+  return r;
 }
 
 template <int V, int U, int THREADS>
@@ -119,6 +152,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   __shared__ uint32_t s_flag;
 
   const int G = gridDim.x, b = blockIdx.x;
+  if (p.trace && b == 0 && threadIdx.x == 0 && p.trace_cap >= 10) p.trace[p.trace_cap - 2] = global_ns();  // entry
   Slice s;
   const int v0 = static_cast<int>(static_cast<int64_t>(b) * p.nvec_total / G);
   const int v1 = static_cast<int>(static_cast<int64_t>(b + 1) * p.nvec_total / G);
@@ -131,6 +165,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
   uint32_t* s_off = reinterpret_cast<uint32_t*>(q);  // [G + 1] prefix of the CTAs' candidate counts
   q += (static_cast<size_t>(G) + 1 + 3) / 4 * 16;
+  uint32_t* ctab = reinterpret_cast<uint32_t*>(q);  // [G * swcap / 32 + 1] region of every 32nd candidate
+  q += (static_cast<size_t>(G) * p.swcap / 32 + 1 + 3) / 4 * 16;
   s.dist = reinterpret_cast<uint32_t*>(q);
   q += static_cast<size_t>(p.swcap) * 4;
   s.pred = reinterpret_cast<int32_t*>(q);
@@ -143,6 +179,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   q += static_cast<size_t>(p.swcap) * 4;
   s.vis = q;
   q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+  uint64_t* bkey = reinterpret_cast<uint64_t*>(q);  // per-column keys of the filtered relaxation
+  q += static_cast<size_t>(p.swcap) * 8;
+  uint64_t* gthr = reinterpret_cast<uint64_t*>(q);  // their row thresholds
+  q += static_cast<size_t>(p.swcap) / 4 * 8;
+  uint32_t* glist = reinterpret_cast<uint32_t*>(q);  // live 4-column groups
+  q += (static_cast<size_t>(p.swcap) / 4 + 3) / 4 * 16;
+  uint32_t* list = reinterpret_cast<uint32_t*>(q);  // staged settled rows
+  q += static_cast<size_t>(p.list_cap) * 4;
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* rings = q;
@@ -176,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   uint32_t phase = 0;
   for (;;) {
     // per-phase timeline of CTA 0 (profiling only): 8 stamps per phase
-    uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap) ? p.trace + 8 * phase
+    uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? p.trace + 8 * phase
                                                                                            : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = global_ns();
     // 1. publish this slice's partial and its candidates (into its own region)
@@ -231,41 +275,63 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     __syncthreads();
     const Decision D = s_dec;
     const int total = static_cast<int>(s_off[G]);
+    build_chunk_table(s_off, G, ctab);
+    __syncthreads();
     if (tr && threadIdx.x == 0) {
       tr[4] = global_ns();
       tr[7] = static_cast<uint64_t>(total);
     }
     if (D.m >= kInf) break;
-    // 4. stream the settled rows through the warps' rings and relax this slice
-    Best<V> best;
-    best_init<V>(best, s, t, D, p.bits_u);
+    // 4. relax this slice with the settled rows: only columns a settled row can
+    //    still change take part.  None: nothing to read; a few: load just those
+    //    groups; otherwise stream the whole slice through the warps' rings.
     const uint4* cl = p.cand + static_cast<size_t>(phase & 1) * G * p.swcap;
     const int swcap = p.swcap;
-    bool ok;
-    if (p.plain) {  // Algorithm 1's single row a: no candidate list to read
-      const uint4 one = make_uint4(D.a, D.m, 0u, 0u);
-      ok = relax_pull<V, U>([one](int) { return one; }, 1, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows,
-                            slot_tb, p.timeout_ns, best);
+    const uint4 one = make_uint4(D.a, D.m, 0u, 0u);  // plain mode: Algorithm 1's single row a
+    auto get = [cl, swcap, s_off, ctab](int i) {
+      const int r = region_at(s_off, ctab, i);
+      return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
+    };
+    const int nlg = p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc) : s.nvec;
+    if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(nlg) << 32;
+    if (nlg <= p.gather_max) {
+      if (nlg > 0) {
+        for (int j = threadIdx.x; j < s.sw; j += blockDim.x) bkey[j] = (static_cast<uint64_t>(s.dist[j]) << 32) | 0xFFFFFFFFu;
+        if (p.plain)
+          relax_gather([one](int) { return one; }, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list,
+                       p.list_cap, bkey, &sc);
+        else
+          relax_gather(get, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey, &sc);
+      }
+      if (tr && threadIdx.x == 0) tr[5] = global_ns();
+      // 5. mark, commit, and the next partial
+      commit_keys(s, D, p.bits_u, nlg > 0 ? bkey : nullptr, key_t, lc_t);
     } else {
-      ok = relax_pull<V, U>(
-          [cl, swcap, G, s_off](int i) {
-            const int r = region_of(s_off, G, i);
-            return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
-          },
-          total, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows, slot_tb, p.timeout_ns, best);
+      Best<V> best;
+      best_init<V>(best, s, t, D, p.bits_u);
+      bool ok;
+      if (p.plain)
+        ok = relax_pull<V, U>([one](int) { return one; }, 1, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows,
+                              slot_tb, p.timeout_ns, best);
+      else
+        ok = relax_pull<V, U>(get, total, s, t, p.W, p.pitch, D, p.bits_u, ring, slot_rows, slot_tb, p.timeout_ns,
+                              best);
+      if (!ok) {
+        atomicOr(p.words, kErrTimeout);
+        atomicExch(abort_flag, 1u);
+      }
+      if (tr && threadIdx.x == 0) tr[5] = global_ns();
+      // 5. merge, mark, commit, and the next partial
+      commit_partial<V>(s, t, D, merge, p.bits_u, best, key_t, lc_t);
     }
-    if (!ok) {
-      atomicOr(p.words, kErrTimeout);
-      atomicExch(abort_flag, 1u);
-    }
-    if (tr && threadIdx.x == 0) tr[5] = global_ns();
-    // 5. merge, mark, commit, and the next partial
-    commit_partial<V>(s, t, D, merge, p.bits_u, best, key_t, lc_t);
     if (tr && threadIdx.x == 0) tr[6] = global_ns();
     ++phase;
   }
   slice_write_out(s, p.n, p.dist_out, p.pred_out);
-  if (b == 0 && threadIdx.x == 0) p.words[1] = phase;
+  if (b == 0 && threadIdx.x == 0) {
+    p.words[1] = phase;
+    if (p.trace && p.trace_cap >= 10) p.trace[p.trace_cap - 1] = global_ns();  // exit
+  }
 }
 
 // ============================================================ cluster engine
@@ -480,7 +546,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
           const int32_t* minin_g = d.minout + d.n;
           const int cnt = stage_settled(
               [Cn, minin_g](int i) {
-                const int r = region_of(s_off, Cn, i);
+                const int r = region_of16(s_off, Cn, i);
                 const uint2 e = ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
                 return make_uint4(e.x, e.y, in_key(e.y, static_cast<uint32_t>(__ldg(minin_g + e.x))), 0u);
               },
@@ -509,8 +575,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
 namespace {
 
 constexpr int kRowsPerStage = 8;  // U: rows per ring stage
+constexpr int kGridListCap = 8192;  // grid engine: staged settled rows per segment
+
 constexpr int kGridThreads = 512;
 constexpr int kClusterThreads = 256;
+
+// Column filter default: load only the live groups when at most a quarter of a
+// slice's 4-column groups (and at least 2) are live.
+int auto_gather_max(int nvec_cta) { return std::min(kGridThreads, std::max(2, nvec_cta / 4)); }
 
 // Shared-memory layout of one CTA (must match the carving in the kernels).
 struct Layout {
@@ -519,7 +591,8 @@ struct Layout {
   int rgs_cap = 0;  // row groups (merge buffer rows)
   int depth = 0;    // ring stages per warp
   int srows = 0;    // rows per stage (<= kRowsPerStage)
-  int list_cap = 0; // cluster engine: staged settled rows per segment
+  int list_cap = 0; // staged settled rows per segment
+  bool filter = false;  // grid engine: per-column keys and live groups of the filtered relaxation
   int rowcap = 0;   // bytes of one ring row slot
   size_t smem = 0;
 };
@@ -527,13 +600,16 @@ struct Layout {
 // own_copies: published candidate lists kept in shared memory (cluster: 2);
 // offs: prefix entries of the grid engine's candidate counts (grid: G + 1).
 size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
-  // L.list_cap: staged settled rows (cluster engine only)
   size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (one row group: unused)
   b += static_cast<size_t>(L.swcap) * 16 * own_copies;                           // published candidates
   b += (static_cast<size_t>(offs) + 3) / 4 * 16;                                 // candidate-count prefix
+  if (offs) b += (static_cast<size_t>(offs - 1) * L.swcap / 32 + 1 + 3) / 4 * 16;  // its chunk table
   b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
   b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
   b += static_cast<size_t>(L.list_cap) * 4;                                      // staged rows
+  if (L.filter)  // per-column keys, group thresholds, live groups
+    b += static_cast<size_t>(L.swcap) * 8 + static_cast<size_t>(L.swcap) / 4 * 8 +
+         (static_cast<size_t>(L.swcap) / 4 + 3) / 4 * 16;
   b += 128;                                                                      // ring alignment
   b += static_cast<size_t>(nwarps) * L.depth * L.srows * L.rowcap;               // TMA rings
   b += static_cast<size_t>(nwarps) * L.depth * 8;                                // mbarriers
@@ -613,6 +689,8 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   const int want_depth = o.unroll > 0 ? std::min(o.unroll, 8) : 2;
   const size_t budget = static_cast<size_t>(ctx->max_smem_optin) / per_sm - 1024;
   Layout L;
+  L.filter = true;
+  L.list_cap = std::min(nvec_total * 4, kGridListCap);
   if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
   void* fn = grid_kernel_for(L.V);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
@@ -659,6 +737,8 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.rowcap = L.rowcap;
   p.trace_cap = o.trace ? o.trace_cap : 0;
   p.trace = o.trace;
+  p.list_cap = L.list_cap;
+  p.gather_max = o.live < 0 ? -1 : o.live > 0 ? std::min(o.live, kGridThreads) : auto_gather_max(nvec_cta);
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   cudaFreeAsync(ws, st);
@@ -909,6 +989,8 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   const int nwarps = kGridThreads / 32;
   const int nvec_cta = (nvec_total + G - 1) / G;
   Layout L;
+  L.filter = true;
+  L.list_cap = std::min(nvec_total * 4, kGridListCap);
   if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, 2, static_cast<size_t>(dv->max_smem_optin) - 1024, &L))
     return rc;
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
@@ -956,6 +1038,8 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.rowcap = L.rowcap;
   p.trace_cap = 0;
   p.trace = nullptr;
+  p.list_cap = L.list_cap;
+  p.gather_max = auto_gather_max(nvec_cta);
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
