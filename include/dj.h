@@ -66,6 +66,7 @@ typedef struct dj_graph_info {
   const int32_t* minout; /* device pointer: n int32, min finite off-diagonal weight of row u (DJ_INF if none) */
   const int32_t* minin;  /* device pointer: n int32, min finite off-diagonal weight of column v (DJ_INF if none) */
   uint64_t bytes;        /* device bytes owned by the graph */
+  uint64_t entries;      /* finite off-diagonal matrix entries (directed edges; twice the undirected ones) */
 } dj_graph_info;
 
 /* Build the n x n matrix on the current device from an edge list (Section
@@ -144,6 +145,13 @@ typedef struct dj_solve_opts {
                              loads only those; > 0: load only the live columns when at most this
                              many 4-column groups of the CTA's slice are live; -1 = off (every
                              settled row's whole slice is streamed). */
+  int32_t rowsplit;       /* grid engine: a phase with at least this many settled candidates streams
+                             whole rows, each CTA a share of them, and merges the per-column bests
+                             through global memory around one more grid barrier (reading a whole
+                             row per CTA streams HBM faster than every CTA reading its slice of
+                             every row).  0 = auto (2048 on graphs with at least n^2/32 finite
+                             entries, never on sparser ones), -1 = never. */
+  int32_t reserved[3];
 } dj_solve_opts;
 
 #define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only */

@@ -135,6 +135,7 @@ extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int3
   if (o.mode < DJ_MODE_AUTO || o.mode > DJ_MODE_PLAIN) return set_error(DJ_EINVAL, "unknown mode");
   if (o.settle < DJ_SETTLE_AUTO || o.settle > DJ_SETTLE_OUT_IN) return set_error(DJ_EINVAL, "unknown settle bounds");
   if (o.live < -1) return set_error(DJ_EINVAL, "live must be -1, 0 or a group count");
+  if (o.rowsplit < -1) return set_error(DJ_EINVAL, "rowsplit must be -1, 0 or a candidate count");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int engine = o.engine;
   if (engine == DJ_ENGINE_AUTO) engine = g->n >= kGridMinN ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;

@@ -26,8 +26,9 @@
 //     orders exactly that way, so the fused pass picks Algorithm 1's pred.
 //   - A final (visited or settled) node can never be strictly improved, so the
 //     relaxation needs no visited test (it is kept in the selection only).
-//   - L is capped at m + 2^(32 - bits(n)) so (dist[u] - m, u) packs into 32
-//     bits; a smaller L only shrinks S, and S always contains a.
+//   - L is capped at m + 2^(32 - bits(n)) - 1 so (dist[u] - m, u) packs into
+//     32 bits below all ones (reserved for "none"); a smaller L only shrinks
+//     S, and S always contains a.
 //   - With every off-diagonal weight >= 1, the "IN" criterion of the same
 //     paper also settles v when dist[v] <= m + minin[v] (minin: the smallest
 //     weight into v): the last edge of a shorter path would have to leave an
@@ -54,6 +55,7 @@ namespace dj {
 struct BlockScratch {
   uint64_t r64[32];
   uint32_t r32[32];
+  uint32_t r32b[32];
   uint32_t cnt[33];
   uint64_t b64;
   uint32_t b32;
@@ -78,7 +80,7 @@ struct Decision {
   uint32_t m;     // smallest unvisited dist (kInf: done)
   uint32_t a;     // its node (smallest index on ties)
   uint32_t L;     // OUT bound: unvisited v with dist[v] < L are settled
-  uint32_t span;  // packing span 2^(32 - bits(n))
+  uint32_t span;  // packing span 2^(32 - bits(n)) - 1
   uint32_t use_in;
 };
 
@@ -134,21 +136,33 @@ __device__ __forceinline__ uint32_t cap_bound(uint64_t key, uint32_t lc, uint32_
   return min(min(lc, mc + span), kInf);
 }
 
-// Per-thread part of a slice's partial: argmin key (dist << 32 | v) and
-// min(dist + minout) over the unvisited columns this thread visits.
-__device__ __forceinline__ void column_partial(const Slice& s, int j, uint64_t& key, uint32_t& lc) {
+// Per-thread part of a slice's partial over the unvisited columns this thread
+// visits: argmin key (dist << 32 | v), min(dist + minout), and their count.
+struct Part {
+  uint64_t key;
+  uint32_t lc;
+  uint32_t nu;
+};
+
+__device__ __forceinline__ void part_init(Part& pt) {
+  pt.key = kNoKey;
+  pt.lc = 0xFFFFFFFFu;
+  pt.nu = 0;
+}
+
+__device__ __forceinline__ void column_partial(const Slice& s, int j, Part& pt) {
   if (!s.vis[j]) {
     const uint32_t d = s.dist[j];
     const uint64_t kj = (static_cast<uint64_t>(d) << 32) | static_cast<uint32_t>(s.c0 + j);
-    key = kj < key ? kj : key;
-    lc = min(lc, d + s.minout[j]);  // <= 2^32 - 2: no wrap
+    pt.key = kj < pt.key ? kj : pt.key;
+    pt.lc = min(pt.lc, d + s.minout[j]);  // <= 2^32 - 2: no wrap
+    ++pt.nu;
   }
 }
 
-__device__ __forceinline__ void slice_partial(const Slice& s, uint64_t& key, uint32_t& lc) {
-  key = kNoKey;
-  lc = 0xFFFFFFFFu;
-  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) column_partial(s, j, key, lc);
+__device__ __forceinline__ void slice_partial(const Slice& s, Part& pt) {
+  part_init(pt);
+  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) column_partial(s, j, pt);
 }
 
 // Step 1: reduce the per-thread partials to the slice's (key, L_c) and append
@@ -164,23 +178,28 @@ __device__ __forceinline__ void put_entry(uint2* out, uint32_t v, uint32_t d, ui
 
 template <class Entry>
 __device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bool plain, bool use_in,
-                                               uint64_t key_t, uint32_t lc_t, Entry* out, BlockScratch* sc,
-                                               uint64_t* key_out, uint32_t* Lc_out) {
+                                               const Part& pt, Entry* out, BlockScratch* sc, uint64_t* key_out,
+                                               uint32_t* Lc_out, uint32_t* unvis_out = nullptr) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  uint64_t k = warp_min_u64(key_t);
-  uint32_t l = warp_min_u32(lc_t);
+  uint64_t k = warp_min_u64(pt.key);
+  uint32_t l = warp_min_u32(pt.lc);
+  uint32_t nu = unvis_out ? warp_sum_u32(pt.nu) : 0u;
   if (lane == 0) {
     sc->r64[w] = k;
     sc->r32[w] = l;
+    sc->r32b[w] = nu;
   }
   __syncthreads();
   k = kNoKey;
   l = 0xFFFFFFFFu;
+  nu = 0;
   for (int i = 0; i < nw; ++i) {  // every thread reduces the warp results itself
     const uint64_t x = sc->r64[i];
     k = x < k ? x : k;
     l = min(l, sc->r32[i]);
+    nu += sc->r32b[i];
   }
+  if (unvis_out) *unvis_out = nu;
   const uint32_t Lc = cap_bound(k, l, span, plain);
   const uint32_t ac = static_cast<uint32_t>(k);
   const uint32_t mc = static_cast<uint32_t>(k >> 32);
@@ -611,26 +630,160 @@ __device__ __forceinline__ void relax_gather(const Get& get, int total, const Sl
   }
 }
 
+// Row-split relaxation (grid engine, phases with many settled rows).  Reading
+// a whole row per CTA streams HBM faster than every CTA reading its slice of
+// every row, at the price of a merge: CTA b takes the settled rows among
+// candidates b, b + G, b + 2G, ... and streams each row over all columns in
+// chunks of 4 T CPT columns.  Thread 0 copies a row's chunk with one TMA bulk
+// copy into shared buffer (g & 1), g counting the CTA's buffered rows over the
+// kernel (rs_gt), so two rows are in flight; thread t keeps the running bests
+// of the chunk's 4-column groups t + T j (j < CPT) in registers.  A best that
+// can commit -- below the column's dist in the snapshot `gsnap` the owners
+// wrote when this phase began, or equal to it where the snapshot's top bit
+// says a tie can still win -- is merged into gkey (64-bit keys
+// (candidate << 32) | tie word, global atomicMin); the owners read their
+// slice of gkey after a grid barrier and commit from it.  The owners announce
+// their snapshots on *snap_count (one release increment per CTA); the first
+// merge waits, bounded, for snap_target of them -- long done by then, since
+// the snapshots are written before the rows are streamed.  Returns false if a
+// copy or that wait did not complete in time.  Ends synced.
+template <int CPT, class Get>
+__device__ __forceinline__ bool relax_rows(const Get& get, int total, int b, int G, const int32_t* __restrict__ W,
+                                           int64_t pitch, const Decision& D, uint32_t bits_u,
+                                           const uint32_t* __restrict__ gsnap, unsigned long long* gkey,
+                                           uint32_t* list, int list_cap, uint8_t* rbuf, uint64_t* rbar,
+                                           uint32_t& rs_gt, int64_t timeout_ns, const uint32_t* snap_count,
+                                           uint32_t snap_target, uint32_t* abort_flag, BlockScratch* sc) {
+  const uint32_t umask = (1u << bits_u) - 1u;
+  if (threadIdx.x == 0) sc->cnt[31] = 0;
+  __syncthreads();
+  // this CTA's share (at most ceil(total / G) <= the slice width <= list_cap rows)
+  for (int k = threadIdx.x; b + G * k < total; k += blockDim.x) {
+    const uint4 e = get(b + G * k);
+    if (in_settled(e.x, e.y, e.z, D)) {
+      const uint32_t at = atomicAdd(&sc->cnt[31], 1u);
+      if (at < static_cast<uint32_t>(list_cap)) list[at] = ((e.y - D.m) << bits_u) | e.x;
+    }
+  }
+  __syncthreads();
+  const int nrows = min(static_cast<int>(sc->cnt[31]), list_cap);
+  const int T = static_cast<int>(blockDim.x);
+  const int nvec = static_cast<int>(pitch / 4);
+  const int chunkv = T * CPT;
+  const size_t bufbytes = static_cast<size_t>(min(chunkv, nvec)) * 16;
+  bool ok = true;
+  for (int c0 = 0; c0 < nvec; c0 += chunkv) {
+    const int cv = min(chunkv, nvec - c0);
+    const uint32_t bytes = static_cast<uint32_t>(cv) * 16u;
+    auto issue = [&](int r) {  // thread 0
+      const uint32_t g = rs_gt + static_cast<uint32_t>(r);
+      const uint32_t u = list[r] & umask;
+      fence_proxy_async_smem();  // earlier generic reads of the buffer precede the copy
+      mbar_arrive_expect_tx(rbar + (g & 1u), bytes);
+      bulk_g2s(rbuf + (g & 1u) * bufbytes, W + static_cast<int64_t>(u) * pitch + 4 * static_cast<int64_t>(c0), bytes,
+               rbar + (g & 1u));
+    };
+    if (threadIdx.x == 0) {
+      if (nrows > 0) issue(0);
+      if (nrows > 1) issue(1);
+    }
+    uint32_t bc[CPT][4], bt[CPT][4];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bc[j][q] = 0xFFFFFFFFu;
+        bt[j][q] = 0xFFFFFFFFu;
+      }
+    for (int r = 0; r < nrows; ++r) {
+      const uint32_t g = rs_gt + static_cast<uint32_t>(r);
+      if (!mbar_wait_bounded(rbar + (g & 1u), (g >> 1) & 1u, timeout_ns)) {
+        ok = false;
+        mbar_wait_bounded(rbar + (g & 1u), (g >> 1) & 1u, timeout_ns);  // drain once more
+      }
+      const uint32_t tb = list[r];
+      const uint32_t du = D.m + (tb >> bits_u);
+      const int4* buf = reinterpret_cast<const int4*>(rbuf + (g & 1u) * bufbytes);
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int gv = static_cast<int>(threadIdx.x) + T * j;
+        if (gv < cv) {
+          const int4 x = buf[gv];
+          best_update(du + static_cast<uint32_t>(x.x), tb, bc[j][0], bt[j][0]);
+          best_update(du + static_cast<uint32_t>(x.y), tb, bc[j][1], bt[j][1]);
+          best_update(du + static_cast<uint32_t>(x.z), tb, bc[j][2], bt[j][2]);
+          best_update(du + static_cast<uint32_t>(x.w), tb, bc[j][3], bt[j][3]);
+        }
+      }
+      __syncthreads();  // buffer (g & 1) is free again
+      if (threadIdx.x == 0 && r + 2 < nrows) issue(r + 2);
+    }
+    rs_gt += static_cast<uint32_t>(nrows);
+    if (c0 == 0) {  // every owner's snapshot is visible before the first merge
+      __shared__ uint32_t s_snap_ok;
+      if (threadIdx.x == 0) {
+        uint32_t okw = 1;
+        if (static_cast<int32_t>(ld_acquire_gpu(snap_count) - snap_target) < 0) {
+          const uint64_t t0 = global_ns();
+          while (static_cast<int32_t>(ld_acquire_gpu(snap_count) - snap_target) < 0) {
+            if (ld_relaxed_gpu(abort_flag) || static_cast<int64_t>(global_ns() - t0) > timeout_ns) {
+              okw = 0;
+              break;
+            }
+          }
+        }
+        s_snap_ok = okw;
+      }
+      __syncthreads();
+      if (!s_snap_ok) {
+        fence_proxy_async_smem();
+        return false;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int gv = static_cast<int>(threadIdx.x) + T * j;
+      if (gv >= cv || (bt[j][0] & bt[j][1] & bt[j][2] & bt[j][3]) == 0xFFFFFFFFu) continue;  // nothing offered
+      const uint4 sn = __ldcg(reinterpret_cast<const uint4*>(gsnap) + c0 + gv);
+      const uint32_t s4[4] = {sn.x, sn.y, sn.z, sn.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t d = s4[q] & 0x7FFFFFFFu;
+        if (bc[j][q] < d || (bc[j][q] == d && (s4[q] >> 31) && bt[j][q] != 0xFFFFFFFFu))
+          atomicMin(gkey + 4 * (c0 + gv) + q, (static_cast<unsigned long long>(bc[j][q]) << 32) | bt[j][q]);
+      }
+    }
+  }
+  fence_proxy_async_smem();  // this thread's reads of the buffers precede later copies into them
+  return ok;
+}
+
+// Snapshot word of column j for relax_rows: dist, with the top bit set when
+// a tie can still replace pred (IN bound on, pred's dist >= this phase's m).
+__device__ __forceinline__ uint32_t snapshot_word(const Slice& s, int j, const Decision& D) {
+  const bool tie = D.use_in && s.pred[j] >= 0 && s.pdist[j] >= D.m && s.dist[j] < kInf;
+  return s.dist[j] | (tie ? 0x80000000u : 0u);
+}
+
 // One column of a commit: mark it visited if it was settled this phase
 // (judged on its state before the commit), commit a lexicographically
 // smaller key b, and fold the column into this thread's next partial.
 __device__ __forceinline__ void commit_column(const Slice& s, int col, uint64_t b, const Decision& D,
-                                              uint32_t bits_u, uint64_t& key, uint32_t& lc) {
+                                              uint32_t bits_u, Part& pt) {
   const uint32_t d = s.dist[col];
   const uint32_t tie0 = stored_tie(s, col, D, bits_u);
   if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
   commit_key(s, col, b, tie0, D, bits_u);
-  column_partial(s, col, key, lc);
+  column_partial(s, col, pt);
 }
 
 // Commit from the per-column keys of relax_gather, or from none (bkey null:
 // no live column in the slice).
 __device__ __forceinline__ void commit_keys(const Slice& s, const Decision& D, uint32_t bits_u, const uint64_t* bkey,
-                                            uint64_t& key, uint32_t& lc) {
-  key = kNoKey;
-  lc = 0xFFFFFFFFu;
+                                            Part& pt) {
+  part_init(pt);
   for (int col = threadIdx.x; col < s.sw; col += blockDim.x)
-    commit_column(s, col, bkey ? bkey[col] : kNoKey, D, bits_u, key, lc);
+    commit_column(s, col, bkey ? bkey[col] : kNoKey, D, bits_u, pt);
 }
 
 // Merge the row groups' bests, then for every column: mark it visited if it
@@ -640,12 +793,10 @@ __device__ __forceinline__ void commit_keys(const Slice& s, const Decision& D, u
 // must be merged.
 template <int V>
 __device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, const Decision& D, uint64_t* merge,
-                                               uint32_t bits_u, const Best<V>& best, uint64_t& key,
-                                               uint32_t& lc) {
+                                               uint32_t bits_u, const Best<V>& best, Part& pt) {
   const int lane = threadIdx.x & 31;
-  key = kNoKey;
-  lc = 0xFFFFFFFFu;
-  auto one = [&](int col, uint64_t b) { commit_column(s, col, b, D, bits_u, key, lc); };
+  part_init(pt);
+  auto one = [&](int col, uint64_t b) { commit_column(s, col, b, D, bits_u, pt); };
   if (t.rgs == 1) {
     if (t.active) {
 #pragma unroll

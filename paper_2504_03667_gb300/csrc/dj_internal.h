@@ -19,6 +19,7 @@ struct dj_graph {
   int32_t* minout = nullptr;  // n row minima (then the n column minima, same allocation)
   int32_t* minin = nullptr;   // n column minima
   uint64_t bytes = 0;
+  uint64_t entries = 0;       // finite off-diagonal matrix entries
 };
 
 namespace dj {
@@ -61,7 +62,10 @@ inline uint32_t host_bits_for(uint32_t n) {
   while (b < 31 && (1u << b) < n) ++b;
   return b;
 }
-inline uint32_t host_span_for(uint32_t n) { return 1u << (32 - host_bits_for(n)); }
+// Packing span of the tie word ((dist - m) << bits) | u: settled rows have
+// dist - m < span.  One below the power of two, so no tie word is all ones
+// (all ones marks "no stored tie" and "no candidate").
+inline uint32_t host_span_for(uint32_t n) { return (1u << (32 - host_bits_for(n))) - 1u; }
 
 SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, int plain);
 

@@ -58,13 +58,15 @@ __global__ void k_copy_dense(int32_t* __restrict__ W, int64_t pitch, const int32
 }
 
 // One warp per row: minout[u] = min finite W[u][v], v != u; plus the global
-// finite min / max (stats[0] = min, stats[1] = max).
+// finite min / max and the number of finite entries (stats[0] = min,
+// stats[1] = max, stats[2..3] = count as a 64-bit word).
 __global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n, int32_t* __restrict__ minout,
                          uint32_t* stats) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   uint32_t gmin = kInf, gmax = 0;
+  unsigned long long cnt = 0;
   for (int64_t u = warp; u < n; u += nwarps) {
     const int32_t* row = W + u * pitch;
     uint32_t mn = kInf, mx = 0;
@@ -73,6 +75,7 @@ __global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
       if (v != u && x < kInf) {
         mn = min(mn, x);
         mx = max(mx, x);
+        ++cnt;
       }
     }
     mn = warp_min_u32(mn);
@@ -82,9 +85,13 @@ __global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
     gmin = min(gmin, mn);
     gmax = max(gmax, mx);
   }
-  if (lane == 0 && stats) {
-    atomicMin(stats, gmin);
-    atomicMax(stats + 1, gmax);
+  if (stats) {
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) {
+      atomicMin(stats, gmin);
+      atomicMax(stats + 1, gmax);
+      atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), cnt);
+    }
   }
 }
 
@@ -180,18 +187,19 @@ static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
 // Row and column minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
 static int finish_graph(dj_graph* g, cudaStream_t st) {
   uint32_t* stats = nullptr;
-  cudaError_t e = cudaMallocAsync(&stats, 2 * sizeof(uint32_t), st);
+  cudaError_t e = cudaMallocAsync(&stats, 4 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(stats)");
-  uint32_t init[2] = {kInf, 0};
+  uint32_t init[4] = {kInf, 0, 0, 0};
   cudaMemcpyAsync(stats, init, sizeof(init), cudaMemcpyHostToDevice, st);
   launch_minima(g, stats, st);
-  uint32_t res[2];
+  uint32_t res[4];
   cudaMemcpyAsync(res, stats, sizeof(res), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(stats, st);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "building the row minima");
   g->wmin = static_cast<int32_t>(res[0]);
   g->wmax = static_cast<int32_t>(res[1]);
+  g->entries = static_cast<uint64_t>(res[2]) | (static_cast<uint64_t>(res[3]) << 32);
   if (g->n > 1 && static_cast<int64_t>(g->n - 1) * g->wmax >= static_cast<int64_t>(DJ_INF))
     return set_error(DJ_EOVERFLOW, "(n-1) * max weight >= INT32_MAX: path lengths could overflow int32");
   return DJ_OK;
@@ -348,6 +356,7 @@ extern "C" int dj_graph_get_info(const dj_graph* g, dj_graph_info* info) {
   info->minout = g->minout;
   info->minin = g->minin;
   info->bytes = g->bytes;
+  info->entries = g->entries;
   return DJ_OK;
 }
 

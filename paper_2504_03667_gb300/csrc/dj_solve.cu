@@ -34,7 +34,7 @@ struct GridParams {
   const int32_t* minout;
   int32_t* dist_out;
   int32_t* pred_out;
-  uint32_t* ctl;  // [0] barrier arrivals, [1..3] candidate counters, [5] abort flag
+  uint32_t* ctl;  // [0] barrier arrivals, [5] abort flag, [8] row-split snapshots published
   uint4* partials;  // [2][G]: (key lo, key hi, L_c, count)
   uint4* cand;      // [2][cand_cap] candidates (u, dist[u], IN key, 0)
   uint32_t* words;  // per-device words: [0] error bits, [1] phases
@@ -58,6 +58,10 @@ struct GridParams {
   uint64_t* trace;   // optional per-phase timeline (CTA 0)
   int32_t list_cap;    // staged settled rows per segment (column-filtered relaxation)
   int32_t gather_max;  // load only the live columns when at most this many groups are live (-1: never filter)
+  int32_t rs_min;      // row-split relaxation for phases with at least this many candidates (0: never)
+  int32_t ring_bytes;  // bytes of the ring region (also the row-split buffers)
+  uint32_t* gsnap;     // [pitch] column snapshots at the start of a row-split phase
+  unsigned long long* gkey;  // [2][pitch] merged row-split keys per phase parity, all ones between uses
 };
 
 // Grid-wide barrier on a monotonic arrival counter (zeroed before launch):
@@ -101,6 +105,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uin
 }
 
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
+constexpr int kRowSplitCpt = 8;          // row split: 4-column groups per thread per column chunk
 
 // The region (publishing CTA) of entry i of a phase's candidate list: the
 // largest r with off[r] <= i < off[r + 1] (off: prefix of the regions'
@@ -189,10 +194,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   q += static_cast<size_t>(p.list_cap) * 4;
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* rings = q;
-  q += static_cast<size_t>(nwarps) * p.depth * p.srows * p.rowcap;
+  uint8_t* rings = q;  // the warps' TMA rings; in row-split phases the two row buffers
+  q += static_cast<size_t>(p.ring_bytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(q);
   q += static_cast<size_t>(nwarps) * p.depth * 8;
+  uint64_t* rbar = reinterpret_cast<uint64_t*>(q);  // the row buffers' mbarriers
+  q += 16;
   uint32_t* slot_rows = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth;
   q += static_cast<size_t>(nwarps) * p.depth * 4;
   uint32_t* slot_tb = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth * U;
@@ -208,16 +215,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
   if (lane == 0)
     for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
-  if (threadIdx.x == 0) sc.cnt[32] = 0;
+  if (threadIdx.x == 0) {
+    sc.cnt[32] = 0;
+    mbar_init(rbar, 1);
+    mbar_init(rbar + 1, 1);
+  }
   fence_mbar_init();
   __syncthreads();
 
   uint32_t* bar = p.ctl;
   uint32_t* abort_flag = p.ctl + 5;
-  uint64_t key_t;
-  uint32_t lc_t;
-  slice_partial(s, key_t, lc_t);
-  uint32_t phase = 0;
+  if (p.rs_min > 0) {  // row-split merge keys of this slice, ordered before use by the first barrier
+    for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+      p.gkey[s.c0 + j] = ~0ull;
+      p.gkey[static_cast<size_t>(p.pitch) + s.c0 + j] = ~0ull;
+    }
+  }
+  Part part;
+  slice_partial(s, part);
+  uint32_t phase = 0, nbar = 0, rs_gt = 0, rs_phases = 0;
+  __shared__ uint32_t s_rem;  // unvisited columns that are no candidates, summed over the CTAs
   for (;;) {
     // per-phase timeline of CTA 0 (profiling only): 8 stamps per phase
     uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? p.trace + 8 * phase
@@ -227,14 +244,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     uint4* out = p.cand + (static_cast<size_t>(phase & 1) * G + b) * p.swcap;
     uint64_t key;
     uint32_t Lc;
-    const int c = publish_partial(s, p.span, p.plain != 0, p.use_in != 0, key_t, lc_t, out, &sc, &key, &Lc);
+    uint32_t unvis = 0;
+    const int c = publish_partial(s, p.span, p.plain != 0, p.use_in != 0, part, out, &sc, &key, &Lc,
+                                  p.rs_min > 0 ? &unvis : nullptr);
+    // with row split on (slices < 2^16 columns): count | (unvisited non-candidates << 16)
+    const uint32_t w4 = p.rs_min > 0 ? static_cast<uint32_t>(c) | ((unvis - static_cast<uint32_t>(c)) << 16)
+                                     : static_cast<uint32_t>(c);
     if (threadIdx.x == 0)
       p.partials[static_cast<size_t>(phase & 1) * G + b] =
-          make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
+          make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, w4);
     // 2. one grid barrier per phase
     if (tr && threadIdx.x == 0) tr[1] = global_ns();
     if (b == p.skip_cta) return;  // testing: this CTA never arrives
-    if (!grid_barrier(bar, (phase + 1) * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag,
+    if (!grid_barrier(bar, ++nbar * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag,
                       tr ? tr + 2 : nullptr))
       return;
     // 3. global decision and the prefix of candidate counts, from the G partials
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       const int per = (G + 31) / 32;  // <= kMaxPartialsPerLane (G <= 320)
       const int i0 = min(G, lane * per), i1 = min(G, i0 + per);
       uint64_t k = kNoKey;
-      uint32_t l = 0xFFFFFFFFu, sum = 0;
+      uint32_t l = 0xFFFFFFFFu, sum = 0, rem = 0;
       const uint4* part = p.partials + static_cast<size_t>(phase & 1) * G;
       uint4 xs[kMaxPartialsPerLane];
 #pragma unroll
@@ -255,7 +277,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
         k = kk < k ? kk : k;
         l = min(l, x.z);
         if (i0 + r < i1) s_off[i0 + r] = sum;
-        sum += x.w;
+        const uint32_t cnt = p.rs_min > 0 ? (x.w & 0xFFFFu) : x.w;
+        sum += cnt;
+        rem += p.rs_min > 0 ? (x.w >> 16) : 0u;
       }
       uint32_t incl = sum;
 #pragma unroll
@@ -267,7 +291,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       if (lane == 31) s_off[G] = incl;
       k = warp_min_u64(k);
       l = warp_min_u32(l);
+      rem = warp_sum_u32(rem);
       if (lane == 0) {
+        s_rem = rem;
         s_dec = make_decision(k, l, p.span, p.plain != 0, p.use_in != 0);
         sc.cnt[32] = 0;  // next publication's counter (every thread has read this one)
       }
@@ -292,9 +318,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       const int r = region_at(s_off, ctab, i);
       return __ldcg(cl + static_cast<size_t>(r) * swcap + (i - static_cast<int>(s_off[r])));
     };
-    const int nlg = p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc) : s.nvec;
-    if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(nlg) << 32;
-    if (nlg <= p.gather_max) {
+    // row split for a big phase after which a fair share of the nodes stays unsettled (otherwise
+    // few columns are live and the filtered paths read less); the same decision in every CTA
+    const bool rowsplit = p.rs_min > 0 && !p.plain && total >= p.rs_min && 16ull * s_rem >= static_cast<uint64_t>(p.n);
+    const int nlg = rowsplit ? 0 : p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc) : s.nvec;
+    if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(rowsplit ? 0xFFFFu : nlg) << 32;
+    if (rowsplit) {
+      unsigned long long* gk = p.gkey + static_cast<size_t>(phase & 1) * p.pitch;
+      // this slice's snapshot for the other CTAs' merges, announced without waiting
+      for (int j = threadIdx.x; j < s.sw; j += blockDim.x) p.gsnap[s.c0 + j] = snapshot_word(s, j, D);
+      __syncthreads();
+      if (threadIdx.x == 0) red_add_release_gpu(p.ctl + 8, 1u);
+      ++rs_phases;
+      if (!relax_rows<kRowSplitCpt>(get, total, b, G, p.W, p.pitch, D, p.bits_u, p.gsnap, gk, list, p.list_cap,
+                                    rings, rbar, rs_gt, p.timeout_ns, p.ctl + 8, rs_phases * static_cast<uint32_t>(G),
+                                    abort_flag, &sc)) {
+        atomicOr(p.words, kErrTimeout);
+        atomicExch(abort_flag, 1u);
+      }
+      // every CTA's merges are in gkey before the owners read their slices
+      if (!grid_barrier(bar, ++nbar * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag))
+        return;
+      for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+        bkey[j] = __ldcg(gk + s.c0 + j);
+        gk[s.c0 + j] = ~0ull;  // reused two phases later, after at least one more barrier
+      }
+      __syncthreads();
+      if (tr && threadIdx.x == 0) tr[5] = global_ns();
+      commit_keys(s, D, p.bits_u, bkey, part);
+    } else if (nlg <= p.gather_max) {
       if (nlg > 0) {
         for (int j = threadIdx.x; j < s.sw; j += blockDim.x) bkey[j] = (static_cast<uint64_t>(s.dist[j]) << 32) | 0xFFFFFFFFu;
         if (p.plain)
@@ -305,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       }
       if (tr && threadIdx.x == 0) tr[5] = global_ns();
       // 5. mark, commit, and the next partial
-      commit_keys(s, D, p.bits_u, nlg > 0 ? bkey : nullptr, key_t, lc_t);
+      commit_keys(s, D, p.bits_u, nlg > 0 ? bkey : nullptr, part);
     } else {
       Best<V> best;
       best_init<V>(best, s, t, D, p.bits_u);
@@ -322,7 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       }
       if (tr && threadIdx.x == 0) tr[5] = global_ns();
       // 5. merge, mark, commit, and the next partial
-      commit_partial<V>(s, t, D, merge, p.bits_u, best, key_t, lc_t);
+      commit_partial<V>(s, t, D, merge, p.bits_u, best, part);
     }
     if (tr && threadIdx.x == 0) tr[6] = global_ns();
     ++phase;
@@ -488,15 +540,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     if (threadIdx.x == 0) sc.cnt[32] = 0;
     __syncthreads();
 
-    uint64_t key_t;
-    uint32_t lc_t;
-    slice_partial(s, key_t, lc_t);
+    Part part;
+    slice_partial(s, part);
     uint32_t phase = 0;
     for (;;) {
       uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
       uint64_t key;
       uint32_t Lc;
-      const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, key_t, lc_t, mine, &sc, &key, &Lc);
+      const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, part, mine, &sc, &key, &Lc);
       if (threadIdx.x == 0)
         s_part[phase & 1] =
             make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
@@ -558,7 +609,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
         }
       }
       if (!ok) atomicOr(p.words, kErrTimeout);
-      commit_partial<V>(s, t, D, merge, d.bits_u, best, key_t, lc_t);
+      commit_partial<V>(s, t, D, merge, d.bits_u, best, part);
       ++phase;
     }
     slice_write_out(s, d.n, d.dist, d.pred);
@@ -576,6 +627,7 @@ namespace {
 
 constexpr int kRowsPerStage = 8;  // U: rows per ring stage
 constexpr int kGridListCap = 8192;  // grid engine: staged settled rows per segment
+constexpr int kRowSplitMin = 2048;  // grid engine: row-split phases from this many candidates on
 
 constexpr int kGridThreads = 512;
 constexpr int kClusterThreads = 256;
@@ -593,9 +645,14 @@ struct Layout {
   int srows = 0;    // rows per stage (<= kRowsPerStage)
   int list_cap = 0; // staged settled rows per segment
   bool filter = false;  // grid engine: per-column keys and live groups of the filtered relaxation
+  size_t rs_bytes = 0;  // grid engine: the two row-split buffers (share the ring region)
   int rowcap = 0;   // bytes of one ring row slot
   size_t smem = 0;
 };
+
+size_t ring_region(const Layout& L, int nwarps) {
+  return std::max(static_cast<size_t>(nwarps) * L.depth * L.srows * L.rowcap, L.rs_bytes);
+}
 
 // own_copies: published candidate lists kept in shared memory (cluster: 2);
 // offs: prefix entries of the grid engine's candidate counts (grid: G + 1).
@@ -611,8 +668,8 @@ size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
     b += static_cast<size_t>(L.swcap) * 8 + static_cast<size_t>(L.swcap) / 4 * 8 +
          (static_cast<size_t>(L.swcap) / 4 + 3) / 4 * 16;
   b += 128;                                                                      // ring alignment
-  b += static_cast<size_t>(nwarps) * L.depth * L.srows * L.rowcap;               // TMA rings
-  b += static_cast<size_t>(nwarps) * L.depth * 8;                                // mbarriers
+  b += ring_region(L, nwarps);                                                   // TMA rings / row buffers
+  b += static_cast<size_t>(nwarps) * L.depth * 8 + 16;                           // mbarriers
   b += static_cast<size_t>(nwarps) * L.depth * (kRowsPerStage + 1) * 4;          // stage row counts + keys
   return b;
 }
@@ -691,7 +748,15 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   Layout L;
   L.filter = true;
   L.list_cap = std::min(nvec_total * 4, kGridListCap);
-  if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
+  // row split pays on dense graphs (few phases, thousands of rows each); auto: density >= 1/32
+  const bool dense = g->entries * 32 >= static_cast<uint64_t>(g->n) * static_cast<uint64_t>(g->n);
+  const bool want_rs = o.mode != DJ_MODE_PLAIN && (o.rowsplit > 0 || (o.rowsplit == 0 && dense));
+  L.rs_bytes = want_rs ? static_cast<size_t>(2) * std::min(nvec_total, kGridThreads * kRowSplitCpt) * 16 : 0;
+  if (make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L) != DJ_OK) {
+    clear_error();
+    L.rs_bytes = 0;  // no room for the row buffers: no row split
+    if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
+  }
   void* fn = grid_kernel_for(L.V);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
@@ -705,8 +770,15 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
   const uint32_t cand_cap = static_cast<uint32_t>(G) * static_cast<uint32_t>(L.swcap);  // one region per CTA
   const size_t cand_bytes = static_cast<size_t>(2) * cand_cap * sizeof(uint4);
+  // row split needs its buffers, a CTA's share of the candidates (<= the slice width) in the
+  // staged list, and slices below 2^16 columns (packed counts in the partials)
+  const int rs_min = (!want_rs || L.rs_bytes == 0 || L.swcap > L.list_cap || L.swcap >= 65536) ? 0
+                     : o.rowsplit > 0                                                         ? o.rowsplit
+                                                                                              : kRowSplitMin;
+  const size_t snap_bytes = rs_min > 0 ? static_cast<size_t>(g->pitch) * 4 : 0;  // pitch is a multiple of 4
+  const size_t gkey_bytes = rs_min > 0 ? static_cast<size_t>(2) * g->pitch * 8 : 0;
   uint8_t* ws = nullptr;
-  e = cudaMallocAsync(&ws, ctl_bytes + part_bytes + cand_bytes, st);
+  e = cudaMallocAsync(&ws, ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(grid workspace)");
   cudaMemsetAsync(ws, 0, ctl_bytes, st);
 
@@ -738,7 +810,15 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.trace_cap = o.trace ? o.trace_cap : 0;
   p.trace = o.trace;
   p.list_cap = L.list_cap;
-  p.gather_max = o.live < 0 ? -1 : o.live > 0 ? std::min(o.live, kGridThreads) : auto_gather_max(nvec_cta);
+  // plain mode relaxes one row per phase: the filter's per-phase pass would cost more than it saves
+  p.gather_max = (o.live < 0 || (o.live == 0 && o.mode == DJ_MODE_PLAIN)) ? -1
+                 : o.live > 0                                              ? std::min(o.live, kGridThreads)
+                                                                           : auto_gather_max(nvec_cta);
+  p.rs_min = rs_min;
+  p.ring_bytes = static_cast<int32_t>(ring_region(L, nwarps));
+  p.gsnap = rs_min > 0 ? reinterpret_cast<uint32_t*>(ws + ctl_bytes + part_bytes + cand_bytes) : nullptr;
+  p.gkey = rs_min > 0 ? reinterpret_cast<unsigned long long*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes)
+                      : nullptr;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   cudaFreeAsync(ws, st);
@@ -1040,6 +1120,10 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.trace = nullptr;
   p.list_cap = L.list_cap;
   p.gather_max = auto_gather_max(nvec_cta);
+  p.rs_min = 0;  // no row-split state in the fixed scratch
+  p.ring_bytes = static_cast<int32_t>(ring_region(L, nwarps));
+  p.gsnap = nullptr;
+  p.gkey = nullptr;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");

@@ -45,7 +45,7 @@ class dj_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("pitch", ctypes.c_int32), ("directed", ctypes.c_int32),
                 ("min_weight", ctypes.c_int32), ("max_weight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("matrix", ctypes.c_void_p), ("minout", ctypes.c_void_p), ("minin", ctypes.c_void_p),
-                ("bytes", ctypes.c_uint64)]
+                ("bytes", ctypes.c_uint64), ("entries", ctypes.c_uint64)]
 
 
 class dj_solve_opts(ctypes.Structure):
@@ -53,7 +53,8 @@ class dj_solve_opts(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("debug_skip_cta", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("trace", ctypes.c_void_p), ("settle", ctypes.c_int32),
-                ("live", ctypes.c_int32)]
+                ("live", ctypes.c_int32), ("rowsplit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class dj_batch_opts(ctypes.Structure):
@@ -272,9 +273,11 @@ def dj_graph_free(g):
 # ---------------------------------------------------------------------- solves
 
 def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, threads=0, ctas_per_sm=0,
-                    unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None, settle=0, live=0) -> dj_solve_opts:
+                    unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None, settle=0, live=0,
+                    rowsplit=0) -> dj_solve_opts:
     """trace: optional int64 CUDA tensor receiving the grid engine's per-phase timeline.
-    live: grid engine column filter (0 auto, -1 off, > 0 gather threshold in 4-column groups)."""
+    live: grid engine column filter (0 auto, -1 off, > 0 gather threshold in 4-column groups).
+    rowsplit: grid engine row-split phases (0 auto, -1 off, > 0 minimum settled candidates)."""
     o = dj_solve_opts()
     load_library().dj_solve_opts_init(ctypes.byref(o))
     o.mode, o.engine, o.cluster_size, o.threads = mode, engine, cluster_size, threads
@@ -283,6 +286,7 @@ def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, th
         o.trace, o.trace_cap = int(trace.data_ptr()), int(trace.numel())
     o.settle = settle
     o.live = live
+    o.rowsplit = rowsplit
     return o
 
 

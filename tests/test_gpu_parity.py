@@ -30,13 +30,13 @@ def dj():
     return _dj
 
 
-def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0):
+def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0, rowsplit=0):
     import torch
     n = dj.dj_graph_get_info(g)["n"]
     dist = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     pred = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     dj.dj_sssp_ex(g, s, dist, pred, dj.make_solve_opts(mode=mode, engine=engine, cluster_size=cluster_size,
-                                                       live=live))
+                                                       live=live, rowsplit=rowsplit))
     dj.dj_sync()
     return dist.cpu().numpy(), pred.cpu().numpy()
 
@@ -157,15 +157,16 @@ def test_complete_equal_weights_and_path(dj, orc):
     assert np.array_equal(d, 3 * np.arange(n)) and np.array_equal(p, np.arange(n) - 1)
 
 
-LIVE = [("ring", -1), ("auto", 0), ("gather", 1 << 20)]
+PATHS = [("ring", -1, -1), ("auto", 0, 0), ("gather", 1 << 20, -1), ("rowsplit", -1, 1)]
 
 
-@pytest.mark.parametrize("live", [v for _, v in LIVE], ids=[n for n, _ in LIVE])
-def test_column_filter_paths(dj, orc, live):
-    """Grid engine column filter: streaming every settled row's slice (ring), the default (skip a
-    slice with no live column, load only the live groups when few), and loading only the live
-    groups in every phase (gather) all give Algorithm 1's dist and pred.  Dense graphs with
-    weights 1..3 make ties on both dist and pred pervasive; zero weights turn the IN bound off."""
+@pytest.mark.parametrize("live,rowsplit", [(lv, rs) for _, lv, rs in PATHS], ids=[n for n, _, _ in PATHS])
+def test_relaxation_paths(dj, orc, live, rowsplit):
+    """Grid engine relaxation paths: streaming every settled row's slice (ring), the default (skip a
+    slice with no live column, load only the live groups when few, row split for big phases),
+    loading only the live groups in every phase (gather), and row split in every phase all give
+    Algorithm 1's dist and pred.  Dense graphs with weights 1..3 make ties on both dist and pred
+    pervasive; zero weights turn the IN bound off."""
     cases = [
         ("dense ties", graphgen.bernoulli(4096, 0.5, 1, 3, seed=91), (0, 1, 2)),
         ("directed ties", graphgen.random_edges(5003, 6 * 5003, 1, 3, seed=92, directed=True), (0, 1)),
@@ -180,7 +181,8 @@ def test_column_filter_paths(dj, orc, live):
             for mode in modes:
                 if mode == 2 and s != 0:
                     continue
-                assert_same(solve(dj, G, s, engine=1, mode=mode, live=live), ref, f"{what} s={s} mode={mode}")
+                assert_same(solve(dj, G, s, engine=1, mode=mode, live=live, rowsplit=rowsplit), ref,
+                            f"{what} s={s} mode={mode}")
         G.free()
 
 
@@ -193,7 +195,8 @@ def test_dense_n16384_full(dj, orc):
     ref = orc.dijkstra(W, s)
     got = solve(dj, G, s)  # the engine and launch the benchmark times
     assert_same(got, ref, "n=16384 p=0.5")
-    assert_same(solve(dj, G, s, engine=1, live=-1), ref, "n=16384 p=0.5, column filter off")
+    assert_same(solve(dj, G, s, engine=1, live=-1, rowsplit=-1), ref, "n=16384 p=0.5, filter and row split off")
+    assert_same(solve(dj, G, s, engine=1, rowsplit=1), ref, "n=16384 p=0.5, row split in every phase")
     assert P.check_invariants(W, s, *got) == []
     assert dj.dj_last_phases() > 0
 
