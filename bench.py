@@ -416,6 +416,24 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
     el = time.perf_counter() - t0
     out["plain_form_n16384"] = {"value": reps / el, "unit": "SSSP/s",
                                 "what": "one node per step (Algorithm 1 literally), one launch per solve, synced"}
+    # the paper's own GPU formulation (label-correcting sweeps, Algorithms 3 and 4) rebuilt
+    # coalesced, on the same workload: exact dist, a shortest-path-tree pred
+    for i in range(3):
+        dj.dj_sssp_lc(g, int(srcs[i]), d, p, stream)
+    dj.dj_sync(stream)
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    lreps = 50
+    l0.record(stream)
+    for i in range(lreps):
+        dj.dj_sssp_lc(g, int(srcs[i % 64]), d, p, stream)
+    l1.record(stream)
+    dj.dj_sync(stream)
+    lms = l0.elapsed_time(l1) / lreps
+    out["label_correcting_n16384"] = {"value": 1e3 / lms, "unit": "SSSP/s", "us_per_solve": 1e3 * lms,
+                                      "sweeps_last_solve": dj.dj_last_phases(),
+                                      "what": "dj_sssp_lc: the paper's sweep-until-no-update CUDA variant, "
+                                              "one cooperative launch per solve"}
     # batched workload: 256 sources of one n=8192 graph in one persistent launch
     bspec = graphgen.WORKLOADS[BATCH_WORKLOAD]
     be = graphgen.make_graph(bspec)

@@ -210,6 +210,19 @@ int dj_last_phases(void);
  * synchronise between them. */
 int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
 
+/* Label-correcting solve: the paper's CUDA variant (Algorithms 3 and 4,
+ * Section III-C), kept as a comparison point for Algorithm 1.  Sweeps relax
+ * every row whose dist changed in the previous sweep until nothing changes
+ * (a Bellman-Ford fixed point), all inside one cooperative kernel with no host
+ * round trip between sweeps.
+ *   g, source, dist, pred, stream: as dj_sssp (dist/pred DEVICE pointers).
+ * dist equals Algorithm 1's exactly.  pred is a shortest-path tree
+ * (dist[pred[v]] + G[pred[v]][v] == dist[v], -1 for the source and unreachable
+ * nodes) but, where several shortest paths exist, not necessarily Algorithm 1's
+ * choice; dj_last_phases() reports the number of sweeps.  Asynchronous; errors
+ * as dj_sssp (DJ_EUNSUPPORTED for slices beyond 512 columns per SM). */
+int dj_sssp_lc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
+
 /* ------------------------------------------------------------------ batched solves */
 /* k solves (graph[i], sources[i]) in ONE persistent launch: one thread-block
  * cluster per solve at a time, solves pulled from a device queue (largest n

@@ -64,90 +64,8 @@ struct GridParams {
   unsigned long long* gkey;  // [2][pitch] merged row-split keys per phase parity, all ones between uses
 };
 
-// Grid-wide barrier on a monotonic arrival counter (zeroed before launch):
-// arrival is a release reduction, waiting an acquire load, so no separate
-// fences are needed.
-// Bounded: after timeout_ns it records kErrTimeout, raises the launch's abort
-// flag and returns false; CTAs already waiting see the flag and leave too.
-__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uint32_t* abort_flag, uint32_t* err,
-                                             int64_t timeout_ns, uint32_t* s_flag, uint64_t* stamps = nullptr) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // release: every write of this CTA ordered before the bar.sync above is
-    // visible to a CTA whose acquire load observes the arrival
-    red_add_release_gpu(bar, 1u);
-    if (stamps) stamps[0] = global_ns();
-    uint32_t ok = 1;
-    if (static_cast<int32_t>(ld_acquire_gpu(bar) - target) < 0) {
-      const uint64_t t0 = global_ns();
-      uint32_t spins = 0;
-      while (static_cast<int32_t>(ld_acquire_gpu(bar) - target) < 0) {
-        if ((++spins & 63u) == 0) {
-          if (ld_relaxed_gpu(abort_flag)) {
-            ok = 0;
-            break;
-          }
-          if (static_cast<int64_t>(global_ns() - t0) > timeout_ns) {
-            atomicOr(err, kErrTimeout);
-            atomicExch(abort_flag, 1u);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    if (ok && ld_relaxed_gpu(abort_flag)) ok = 0;
-    if (stamps) stamps[1] = global_ns();
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
 constexpr int kRowSplitCpt = 8;          // row split: 4-column groups per thread per column chunk
-
-// The region (publishing CTA) of entry i of a phase's candidate list: the
-// largest r with off[r] <= i < off[r + 1] (off: prefix of the regions'
-// counts).  Branch-free fixed-depth search (nreg <= 512).
-__device__ __forceinline__ int region_of(const uint32_t* off, int nreg, int i) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 256; step >= 1; step >>= 1) {
-    const int c = lo + step;
-    lo = (c < nreg && static_cast<int>(off[min(c, nreg - 1)]) <= i) ? c : lo;
-  }
-  return lo;
-}
-
-// region_of for a cluster's lists (nreg <= 16).
-__device__ __forceinline__ int region_of16(const uint32_t* off, int nreg, int i) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 8; step >= 1; step >>= 1) {
-    const int c = lo + step;
-    lo = (c < nreg && static_cast<int>(off[min(c, nreg - 1)]) <= i) ? c : lo;
-  }
-  return lo;
-}
-
-// Chunk table of a candidate list: ctab[c] = region of entry 32 c.  Built by
-// threads r < nreg in parallel from the prefix off; every chunk start lies in
-// exactly one non-empty region.
-__device__ __forceinline__ void build_chunk_table(const uint32_t* off, int nreg, uint32_t* ctab) {
-  for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
-    const uint32_t a = off[r], b = off[r + 1];
-    for (uint32_t c = (a + 31) >> 5; (c << 5) < b; ++c) ctab[c] = static_cast<uint32_t>(r);
-  }
-}
-
-// region_of through the chunk table: a start region, then a walk past region
-// ends (empty regions included) up to entry i.
-__device__ __forceinline__ int region_at(const uint32_t* off, const uint32_t* ctab, int i) {
-  int r = static_cast<int>(ctab[i >> 5]);
-  while (static_cast<int>(off[r + 1]) <= i) ++r;
-  return r;
-}
 
 template <int V, int U, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {

@@ -101,6 +101,7 @@ SIGNATURES = {
     "dj_sssp_ex": (_INT, [_P, _I32, _P, _P, ctypes.POINTER(dj_solve_opts), _U64]),
     "dj_sssp_host": (_INT, [_P, _I32, _P, _P, _U64]),
     "dj_sssp_noalloc": (_INT, [_P, _I32, _P, _P, _U64]),
+    "dj_sssp_lc": (_INT, [_P, _I32, _P, _P, _U64]),
     "dj_sync": (_INT, [_U64]),
     "dj_last_phases": (_INT, []),
     "dj_sssp_batch": (_INT, [_P, _P, _I32, _P, _P, _U64]),
@@ -318,6 +319,11 @@ def dj_sssp_host(g, source: int, dist_host=None, pred_host=None, stream=None):
 def dj_sssp_noalloc(g, source: int, dist, pred, stream=None):
     """Solve without allocating device memory (fixed scratch array in the library)."""
     _check(load_library().dj_sssp_noalloc(_gh(g), int(source), _dptr(dist), _dptr(pred), _stream(stream)))
+
+
+def dj_sssp_lc(g, source: int, dist, pred, stream=None):
+    """Label-correcting solve (the paper's CUDA variant): exact dist, pred a shortest-path tree."""
+    _check(load_library().dj_sssp_lc(_gh(g), int(source), _dptr(dist), _dptr(pred), _stream(stream)))
 
 
 def dj_sync(stream=None):
