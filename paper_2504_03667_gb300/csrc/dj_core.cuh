@@ -184,6 +184,30 @@ __device__ __forceinline__ void slice_init(const Slice& s, int n, int source, co
   }
 }
 
+// Algorithm 1's first step, done at initialisation: every node but the source
+// is at INF, so the first pass settles exactly the source and relaxes its row
+// -- dist[v] = G[s][v] with pred s wherever that is finite (the diagonal never
+// improves the source's own 0).  Call after slice_init; ends synced.
+__device__ __forceinline__ void slice_settle_source(const Slice& s, int n, int source,
+                                                    const int32_t* __restrict__ W, int64_t pitch) {
+  const int32_t* row = W + static_cast<int64_t>(source) * pitch + s.c0;
+  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+    const int v = s.c0 + j;
+    if (v >= n) continue;
+    if (v == source) {
+      s.vis[j] = 1;
+      continue;
+    }
+    const uint32_t w = static_cast<uint32_t>(__ldg(row + j));
+    if (w < kInf) {
+      s.dist[j] = w;
+      s.pred[j] = source;
+      s.pdist[j] = 0u;
+    }
+  }
+  __syncthreads();
+}
+
 // Block-wide min of (key64, val32); every thread gets the result.  Ends synced.
 __device__ __forceinline__ void block_min2(uint64_t& k, uint32_t& l, BlockScratch* sc) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;

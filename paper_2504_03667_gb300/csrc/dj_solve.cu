@@ -123,6 +123,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   uint32_t* slot_tb = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth * U;
 
   slice_init(s, p.n, p.source, p.minout, p.minout + p.n, !p.plain, p.use_in && !p.plain);
+  if (!p.plain) {
+    __syncthreads();
+    slice_settle_source(s, p.n, p.source, p.W, p.pitch);
+  }
   const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
   Ring ring;
   ring.buf = rings + static_cast<size_t>(warp) * p.depth * p.srows * p.rowcap;
@@ -453,6 +457,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     s.nvec = v1 - v0;
     s.sw = 4 * s.nvec;
     slice_init(s, d.n, d.source, d.minout, d.minout + d.n, !d.plain, d.use_in && !d.plain);
+    if (!d.plain) {
+      __syncthreads();
+      slice_settle_source(s, d.n, d.source, d.W, d.pitch);
+    }
     const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
     ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
     if (threadIdx.x == 0) sc.cnt[32] = 0;
