@@ -67,7 +67,12 @@ typedef struct dj_graph_info {
   const int32_t* minin;  /* device pointer: n int32, min finite off-diagonal weight of column v (DJ_INF if none) */
   uint64_t bytes;        /* device bytes owned by the graph */
   uint64_t entries;      /* finite off-diagonal matrix entries (directed edges; twice the undirected ones) */
+  int32_t format;        /* DJ_FORMAT_DENSE (matrix) or DJ_FORMAT_CSR (compressed rows, matrix NULL) */
+  int32_t reserved;
 } dj_graph_info;
+
+#define DJ_FORMAT_DENSE 0
+#define DJ_FORMAT_CSR 1
 
 /* Build the n x n matrix on the current device from an edge list (Section
  * III: edge lists are written into the adjacency matrix; Section III-A
@@ -85,6 +90,20 @@ typedef struct dj_graph_info {
  * ((n-1) * max weight >= INT32_MAX), DJ_ENOMEM, DJ_ECUDA. */
 int dj_load_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
                   int directed, uint64_t stream, dj_graph** out);
+
+/* The same graph kept in compressed-row form only: no n x n matrix (the paper
+ * names that matrix's n^2 memory as the limit for sparse graphs, Section IV
+ * and Conclusion).  Arguments, validation and fill rules as dj_load_edges
+ * (repeats keep their smallest weight, self-loops are dropped, undirected
+ * graphs store both directions); the edges are sorted on the host and the
+ * device holds n + 1 64-bit row offsets, the targets and the weights
+ * (8 bytes per directed edge) plus the row and column minima.  dj_sssp and
+ * dj_sssp_ex solve it with the same phase logic and give the same dist and
+ * pred as on the dense matrix; dj_graph_download / upload, dj_sssp_noalloc,
+ * dj_sssp_lc, batches and serving need the matrix and return
+ * DJ_EUNSUPPORTED.  Synchronous (uploads from host vectors). */
+int dj_load_edges_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                      int directed, uint64_t stream, dj_graph** out);
 
 /* Build a graph from an n x n row-major matrix W with row stride ld >= n
  * (same entry rules as above: diagonal must be 0, entries in [0, DJ_INF]).

@@ -137,6 +137,7 @@ extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int3
   if (o.live < -1) return set_error(DJ_EINVAL, "live must be -1, 0 or a group count");
   if (o.rowsplit < -1) return set_error(DJ_EINVAL, "rowsplit must be -1, 0 or a candidate count");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (g->format == DJ_FORMAT_CSR) return launch_csr(g, source, dist, pred, o, st);
   int engine = o.engine;
   if (engine == DJ_ENGINE_AUTO) engine = g->n >= kGridMinN ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;
   if (engine == DJ_ENGINE_GRID) return launch_grid(g, source, dist, pred, o, st);
@@ -389,6 +390,7 @@ static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, in
     if (!g || !dist[i] || !pred[i]) return set_error(DJ_EINVAL, "NULL graph or result pointer at " + std::to_string(i));
     if (g->device != device) return set_error(DJ_EINVAL, "graph on another device");
     if (sources[i] < 0 || sources[i] >= g->n) return set_error(DJ_EINVAL, "source outside [0, n) at " + std::to_string(i));
+    if (int rc = require_dense(g)) return rc;
     (*h)[i] = make_desc(g, sources[i], dist[i], pred[i], plain);
     *max_n = std::max(*max_n, g->n);
     *max_pitch = std::max(*max_pitch, g->pitch);

@@ -19,7 +19,12 @@ struct dj_graph {
   int32_t* minout = nullptr;  // n row minima (then the n column minima, same allocation)
   int32_t* minin = nullptr;   // n column minima
   uint64_t bytes = 0;
-  uint64_t entries = 0;       // finite off-diagonal matrix entries
+  uint64_t entries = 0;       // finite off-diagonal matrix entries (directed edges)
+  int32_t format = DJ_FORMAT_DENSE;  // DJ_FORMAT_CSR: no matrix, the arrays below
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;  // n + 1 edge offsets
+  int32_t* col = nullptr;      // nnz targets, sorted within a row
+  int32_t* wt = nullptr;       // nnz weights
 };
 
 namespace dj {
@@ -72,6 +77,11 @@ SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* p
 // engines (dj_solve.cu)
 int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
                 cudaStream_t st);
+// compressed-row graphs (dj_csr.cu)
+int launch_csr(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
+               cudaStream_t st);
+// DJ_EUNSUPPORTED for a graph without a dense matrix (entry points that stream matrix rows)
+int require_dense(const dj_graph* g);
 struct ClusterLaunch {
   int cluster_size = 8;
   int threads = 256;

@@ -237,6 +237,7 @@ extern "C" int dj_sssp_lc(const dj_graph* g, int32_t source, int32_t* dist, int3
   clear_error();
   if (!g || !dist || !pred) return set_error(DJ_EINVAL, "NULL argument");
   if (source < 0 || source >= g->n) return set_error(DJ_EINVAL, "source outside [0, n)");
+  if (int rc = require_dense(g)) return rc;
   DevCtx* ctx = nullptr;
   if (int rc = get_ctx(&ctx)) return rc;
   if (!ctx->coop) return set_error(DJ_EUNSUPPORTED, "device lacks cooperative launch");

@@ -318,6 +318,7 @@ extern "C" int dj_load_dense(int32_t n, const int32_t* W, int64_t ld, int w_on_d
 
 extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64_t stream) {
   clear_error();
+  if (int rc = require_dense(g)) return rc;
   if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
@@ -332,6 +333,7 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
 
 extern "C" int dj_graph_download(const dj_graph* g, int32_t* W, int64_t ld, uint64_t stream) {
   clear_error();
+  if (int rc = require_dense(g)) return rc;
   if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpy2DAsync(W, static_cast<size_t>(ld) * sizeof(int32_t), g->W,
@@ -357,6 +359,7 @@ extern "C" int dj_graph_get_info(const dj_graph* g, dj_graph_info* info) {
   info->minin = g->minin;
   info->bytes = g->bytes;
   info->entries = g->entries;
+  info->format = g->format;
   return DJ_OK;
 }
 
@@ -365,6 +368,17 @@ extern "C" int dj_graph_free(dj_graph* g) {
   if (!g) return DJ_OK;
   cudaFree(g->W);
   cudaFree(g->minout);  // minin shares this allocation
+  cudaFree(g->row_ptr);
+  cudaFree(g->col);
+  cudaFree(g->wt);
   delete g;
   return DJ_OK;
 }
+
+namespace dj {
+int require_dense(const dj_graph* g) {
+  if (g && g->format != DJ_FORMAT_DENSE)
+    return set_error(DJ_EUNSUPPORTED, "this call needs the dense matrix; the graph was loaded in compressed-row form");
+  return DJ_OK;
+}
+}  // namespace dj

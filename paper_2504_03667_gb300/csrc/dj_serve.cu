@@ -294,6 +294,7 @@ extern "C" int dj_serve_add_graph(dj_server* s, const dj_graph* g, int32_t* grap
   clear_error();
   if (!s || !g || !graph_id) return set_error(DJ_EINVAL, "NULL argument");
   if (g->device != s->device) return set_error(DJ_EINVAL, "graph on another device");
+  if (int rc = require_dense(g)) return rc;
   if (s->graph_bytes + s->pool_bytes + s->fixed_bytes + g->bytes > s->opts.hbm_budget)
     return set_error(DJ_ENOMEM, "graph does not fit the serving HBM budget");
   s->graphs.push_back(g);

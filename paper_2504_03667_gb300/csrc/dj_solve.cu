@@ -985,6 +985,7 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   clear_error();
   if (!g || !dist || !pred) return set_error(DJ_EINVAL, "NULL argument");
   if (source < 0 || source >= g->n) return set_error(DJ_EINVAL, "source outside [0, n)");
+  if (int rc = require_dense(g)) return rc;
   NoAllocDevice* dv = nullptr;
   if (int rc = noalloc_setup(&dv)) return rc;
   if (!dv->coop) return set_error(DJ_EUNSUPPORTED, "device lacks cooperative launch");

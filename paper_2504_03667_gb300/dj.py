@@ -33,6 +33,7 @@ DJ_INF = 2**31 - 1
 DJ_MODE_AUTO, DJ_MODE_PHASE, DJ_MODE_PLAIN = 0, 1, 2
 DJ_ENGINE_AUTO, DJ_ENGINE_GRID, DJ_ENGINE_CLUSTER = 0, 1, 2
 DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN = 0, 1, 2
+DJ_FORMAT_DENSE, DJ_FORMAT_CSR = 0, 1
 
 
 class DjError(RuntimeError):
@@ -45,7 +46,8 @@ class dj_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("pitch", ctypes.c_int32), ("directed", ctypes.c_int32),
                 ("min_weight", ctypes.c_int32), ("max_weight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("matrix", ctypes.c_void_p), ("minout", ctypes.c_void_p), ("minin", ctypes.c_void_p),
-                ("bytes", ctypes.c_uint64), ("entries", ctypes.c_uint64)]
+                ("bytes", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("format", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class dj_solve_opts(ctypes.Structure):
@@ -91,6 +93,7 @@ SIGNATURES = {
     "dj_status_string": (ctypes.c_char_p, [_INT]),
     "dj_version": (_INT, []),
     "dj_load_edges": (_INT, [_I32, _I64, _P, _P, _P, _INT, _U64, ctypes.POINTER(_P)]),
+    "dj_load_edges_csr": (_INT, [_I32, _I64, _P, _P, _P, _INT, _U64, ctypes.POINTER(_P)]),
     "dj_load_dense": (_INT, [_I32, _P, _I64, _INT, _U64, ctypes.POINTER(_P)]),
     "dj_graph_upload": (_INT, [_P, _P, _I64, _U64]),
     "dj_graph_download": (_INT, [_P, _P, _I64, _U64]),
@@ -221,6 +224,17 @@ def dj_load_edges(n: int, src, dst, w, directed: bool, stream=None) -> Graph:
     out = _P()
     _check(load_library().dj_load_edges(int(n), int(s.shape[0]), s.ctypes.data, d.ctypes.data, ww.ctypes.data,
                                         int(bool(directed)), _stream(stream), ctypes.byref(out)))
+    return Graph(out.value)
+
+
+def dj_load_edges_csr(n: int, src, dst, w, directed: bool, stream=None) -> Graph:
+    """The same graph in compressed-row form only (no n x n matrix); dj_sssp solves it."""
+    s, d, ww = _host_i32(src), _host_i32(dst), _host_i32(w)
+    if not (s.shape == d.shape == ww.shape) or s.ndim != 1:
+        raise ValueError("src, dst, w must be 1-D arrays of equal length")
+    out = _P()
+    _check(load_library().dj_load_edges_csr(int(n), int(s.shape[0]), s.ctypes.data, d.ctypes.data,
+                                            ww.ctypes.data, int(bool(directed)), _stream(stream), ctypes.byref(out)))
     return Graph(out.value)
 
 
