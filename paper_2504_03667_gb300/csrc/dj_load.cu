@@ -321,10 +321,14 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
   if (int rc = require_dense(g)) return rc;
   if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
-                                    static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
-                                    static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(upload)");
+  cudaError_t e;
+  if (ld == g->n && g->n == g->pitch)  // no padding columns on either side: one contiguous copy
+    e = cudaMemcpyAsync(g->W, W, static_cast<size_t>(g->n) * g->pitch * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  else
+    e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
+                          static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
+                          static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "host-to-device matrix copy (upload)");
   launch_minima(g, nullptr, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "row minima");
