@@ -260,8 +260,14 @@ typedef struct dj_batch_opts {
   int32_t threads;       /* 0 = auto */
   int32_t clusters;      /* clusters resident at once, 0 = as many as fit */
   int32_t settle;        /* DJ_SETTLE_* (defined below), 0 = auto */
-  int32_t reserved[7];
+  int32_t copies;        /* DJ_COPIES_*: how a CTA's ring copies its slice of a settled row */
+  int32_t reserved[6];
 } dj_batch_opts;
+
+#define DJ_COPIES_AUTO 0   /* wide where the slice allows it */
+#define DJ_COPIES_NARROW 1 /* every warp copies its own 512-byte part of each row */
+#define DJ_COPIES_WIDE 2   /* a warp copies 2 KB (four 4-column groups per lane) of its rows; row groups
+                              merge through shared-memory atomics.  Larger copies stream faster per SM. */
 
 void dj_batch_opts_init(dj_batch_opts* opts);
 

@@ -248,6 +248,7 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
   dj_batch_opts o;
   dj_batch_opts_init(&o);
   if (opts) o = *opts;
+  if (o.copies < DJ_COPIES_AUTO || o.copies > DJ_COPIES_WIDE) return set_error(DJ_EINVAL, "unknown copies");
   DevCtx* ctx = nullptr;
   if (int rc = get_ctx(&ctx)) return rc;
   std::vector<SolveDesc> h;
@@ -280,6 +281,7 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
   b->cl.cluster_size = o.cluster_size > 0 ? o.cluster_size : 0;
   b->cl.threads = 256;
   b->cl.clusters = o.clusters;
+  b->cl.copies = o.copies;
   if (b->cl.cluster_size == 0) {
     TuneKey key{n_bucket(max_n), 0, ctx->num_sms};
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -898,12 +898,38 @@ __device__ __forceinline__ void commit_keys(const Slice& s, const Decision& D, u
 // commit a lexicographically smaller key, and fold the column into this
 // thread's part of the next partial.  Starts with a barrier when row groups
 // must be merged.
+// With `amerge` the row groups' bests meet in merge[col] (one key per column,
+// kNoKey between phases) by shared-memory atomicMin instead of one merge row
+// per row group.
 template <int V>
 __device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, const Decision& D, uint64_t* merge,
-                                               uint32_t bits_u, const Best<V>& best, Part& pt) {
+                                               uint32_t bits_u, const Best<V>& best, Part& pt, bool amerge = false) {
   const int lane = threadIdx.x & 31;
   part_init(pt);
   auto one = [&](int col, uint64_t b) { commit_column(s, col, b, D, bits_u, pt); };
+  if (amerge && t.rgs > 1) {
+    if (t.active) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int jv = (t.wc * V + k) * 32 + lane;
+        if (jv < s.nvec) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint64_t key = (static_cast<uint64_t>(best.bc[k][c]) << 32) | best.bt[k][c];
+            unsigned long long* slot = reinterpret_cast<unsigned long long*>(merge + 4 * jv + c);
+            if (key < *slot) atomicMin(slot, static_cast<unsigned long long>(key));
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int col = threadIdx.x; col < s.sw; col += blockDim.x) {
+      const uint64_t b = merge[col];
+      merge[col] = kNoKey;  // ready for the next phase (several barriers away)
+      one(col, b);
+    }
+    return;
+  }
   if (t.rgs == 1) {
     if (t.active) {
 #pragma unroll

@@ -86,6 +86,7 @@ struct ClusterLaunch {
   int cluster_size = 8;
   int threads = 256;
   int clusters = 0;  // 0 = as many as fit
+  int copies = 0;    // DJ_COPIES_*: row-slice copy width of the rings (0 = auto)
 };
 // Launch the cluster engine over k descriptors already on the device.
 // `queue` is a device word zeroed by this call before the launch.
@@ -105,6 +106,7 @@ struct ClusterPlan {
   int srows = 0;
   int rowcap = 0;
   int list_cap = 0;
+  int amerge = 0;  // row groups merge through shared-memory atomicMin into one key per column
   uint32_t* words = nullptr;
 };
 int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve = false);

@@ -380,6 +380,7 @@ struct ClusterParams {
   int32_t srows;
   int32_t rowcap;
   int32_t list_cap;  // staged settled rows per segment
+  int32_t amerge;    // row groups merge through atomicMin into one key per column
 };
 
 template <int V, int U, int THREADS, class Jobs>
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   const int nwarps = static_cast<int>(blockDim.x >> 5);
   uint8_t* q = smem;
   uint64_t* merge = reinterpret_cast<uint64_t*>(q);
-  q += p.rgs_cap > 1 ? static_cast<size_t>(p.rgs_cap) * p.swcap * 8 : 0;
+  q += p.rgs_cap > 1 ? static_cast<size_t>(p.amerge ? 1 : p.rgs_cap) * p.swcap * 8 : 0;
   uint2* own = reinterpret_cast<uint2*>(q);  // [2][swcap] (v, dist[v]), read by the other CTAs of the cluster
   q += static_cast<size_t>(p.swcap) * 16;
   Slice s;
@@ -432,6 +433,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   ring.gt = 0;
   if (lane == 0)
     for (int i = 0; i < p.depth; ++i) mbar_init(ring.bar + i, 1);
+  if (p.amerge && p.rgs_cap > 1)
+    for (int j = threadIdx.x; j < p.swcap; j += blockDim.x) merge[j] = kNoKey;
   fence_mbar_init();
   __syncthreads();
 
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
         }
       }
       if (!ok) atomicOr(p.words, kErrTimeout);
-      commit_partial<V>(s, t, D, merge, d.bits_u, best, part);
+      commit_partial<V>(s, t, D, merge, d.bits_u, best, part, p.amerge != 0);
       ++phase;
     }
     slice_write_out(s, d.n, d.dist, d.pred);
@@ -571,6 +574,7 @@ struct Layout {
   int srows = 0;    // rows per stage (<= kRowsPerStage)
   int list_cap = 0; // staged settled rows per segment
   bool filter = false;  // grid engine: per-column keys and live groups of the filtered relaxation
+  bool amerge = false;  // row groups merge by atomicMin into one key per column (no merge rows)
   size_t rs_bytes = 0;  // grid engine: the two row-split buffers (share the ring region)
   int rowcap = 0;   // bytes of one ring row slot
   size_t smem = 0;
@@ -583,7 +587,7 @@ size_t ring_region(const Layout& L, int nwarps) {
 // own_copies: published candidate lists kept in shared memory (cluster: 2);
 // offs: prefix entries of the grid engine's candidate counts (grid: G + 1).
 size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
-  size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.rgs_cap) * L.swcap * 8 : 0;  // merge (one row group: unused)
+  size_t b = L.rgs_cap > 1 ? static_cast<size_t>(L.amerge ? 1 : L.rgs_cap) * L.swcap * 8 : 0;  // merge
   b += static_cast<size_t>(L.swcap) * 16 * own_copies;                           // published candidates
   b += (static_cast<size_t>(offs) + 3) / 4 * 16;                                 // candidate-count prefix
   if (offs) b += (static_cast<size_t>(offs - 1) * L.swcap / 32 + 1 + 3) / 4 * 16;  // its chunk table
@@ -613,8 +617,9 @@ int pick_v(int nvec_cta, int nwarps) {
 
 // Fit the layout into `budget` bytes: the deepest ring up to want_depth stages,
 // with the longest stages (up to kRowsPerStage rows) that fit at that depth.
-int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_depth, size_t budget, Layout* L) {
-  L->V = pick_v(nvec_cta, nwarps);
+int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_depth, size_t budget, Layout* L,
+                int force_v = 0) {
+  L->V = force_v ? force_v : pick_v(nvec_cta, nwarps);
   if (!L->V) return set_error(DJ_EUNSUPPORTED, "graph too large for this engine configuration");
   L->swcap = 4 * std::max(nvec_cta, 1);
   const int wpr = std::max(1, (nvec_cta + 32 * L->V - 1) / (32 * L->V));
@@ -762,6 +767,18 @@ static int cluster_layout(int32_t max_pitch, const ClusterLaunch& cl, Layout* L)
   // two CTAs per SM when they fit, so clusters of different solves share SMs
   const size_t half = static_cast<size_t>(ctx->max_smem_optin) / 2 - 1024;
   L->list_cap = std::min(max_pitch, 512);
+  // wide copies: four 4-column groups per lane, so a warp copies 2 KB of each of its rows (larger
+  // TMA copies stream faster per SM); its row groups merge by atomicMin, two CTAs per SM
+  const bool wide = cl.copies == DJ_COPIES_WIDE || (cl.copies == DJ_COPIES_AUTO && nvec_cta >= 256);
+  if (wide && nvec_cta >= 128 && (nvec_cta + 127) / 128 < nwarps) {
+    Layout W = *L;
+    W.amerge = true;
+    if (make_layout(nvec_cta, nwarps, 1, 0, 2, half, &W, 4) == DJ_OK && W.srows >= 2) {
+      *L = W;
+      return DJ_OK;
+    }
+    clear_error();
+  }
   // full 8-row stages first (short stages stream markedly slower); two CTAs per SM if that still fits
   // two 8-byte candidate lists = one 16-byte "copy" in the layout arithmetic
   if (make_layout(nvec_cta, nwarps, 1, 0, 2, half, L) == DJ_OK && L->srows == kRowsPerStage) return DJ_OK;
@@ -835,6 +852,7 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   plan->srows = L.srows;
   plan->rowcap = L.rowcap;
   plan->list_cap = L.list_cap;
+  plan->amerge = L.amerge ? 1 : 0;
   plan->words = ctx->words;
   return DJ_OK;
 }
@@ -867,6 +885,7 @@ static ClusterParams params_of(const ClusterPlan& plan) {
   p.srows = plan.srows;
   p.rowcap = plan.rowcap;
   p.list_cap = plan.list_cap;
+  p.amerge = plan.amerge;
   return p;
 }
 

@@ -34,6 +34,7 @@ DJ_MODE_AUTO, DJ_MODE_PHASE, DJ_MODE_PLAIN = 0, 1, 2
 DJ_ENGINE_AUTO, DJ_ENGINE_GRID, DJ_ENGINE_CLUSTER = 0, 1, 2
 DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN = 0, 1, 2
 DJ_FORMAT_DENSE, DJ_FORMAT_CSR = 0, 1
+DJ_COPIES_AUTO, DJ_COPIES_NARROW, DJ_COPIES_WIDE = 0, 1, 2
 
 
 class DjError(RuntimeError):
@@ -61,7 +62,8 @@ class dj_solve_opts(ctypes.Structure):
 
 class dj_batch_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("clusters", ctypes.c_int32), ("settle", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("clusters", ctypes.c_int32), ("settle", ctypes.c_int32), ("copies", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class dj_serve_opts(ctypes.Structure):
@@ -382,10 +384,11 @@ class Batch:
 
 
 def dj_batch_create(graphs: Sequence, sources, dists: Sequence, preds: Sequence, mode=DJ_MODE_AUTO,
-                    cluster_size=0, clusters=0, settle=DJ_SETTLE_AUTO) -> Batch:
+                    cluster_size=0, clusters=0, settle=DJ_SETTLE_AUTO, copies=0) -> Batch:
+    """copies: DJ_COPIES_AUTO (0), DJ_COPIES_NARROW (1) or DJ_COPIES_WIDE (2) ring copies."""
     o = dj_batch_opts()
     load_library().dj_batch_opts_init(ctypes.byref(o))
-    o.mode, o.cluster_size, o.clusters, o.settle = mode, cluster_size, clusters, settle
+    o.mode, o.cluster_size, o.clusters, o.settle, o.copies = mode, cluster_size, clusters, settle, copies
     k = len(graphs)
     g = _ptr_array([_gh(x) for x in graphs])
     s = _host_i32(sources)
