@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOAD = "dense_n16384_p0.5"
+METRIC = "SSSP/s (single-source dense Dijkstra, n=16384) and HBM GB/s vs 8 TB/s"
 BATCH_WORKLOAD = "multisource_n8192_p0.05_k256"
 INF = 2**31 - 1
 
@@ -183,12 +184,13 @@ def run_reference(args):
             break
     el = time.perf_counter() - t0
     v = done / el
-    line = {"impl": "reference", "metric": "SSSP/s (single-source dense Dijkstra, n=16384)", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "SSSP/s", "n_gpus": args.gpus, "steps": done, "steps_requested": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "n": e.n, "p": spec.get("p"), "weights": [spec["wlo"], spec["whi"]],
-                       "seed": spec["seed"], "l2": "inputs larger than L2 (1 GiB matrix)"},
+                       "seed": spec["seed"], "sources": "64 seeded distinct, cycled",
+                       "l2": "inputs larger than L2 (1 GiB matrix)", "parallelism": "one host core"},
             "cpu_baseline": {"value": v, "unit": "SSSP/s", "cores": 1, "kind": "oracle",
                              "sample": f"{done} serial Algorithm 1 solves (plain C, 1 thread) at n={e.n}"},
             "e2e": {"value": v, "unit": "SSSP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -296,7 +298,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "SSSP/s (single-source dense Dijkstra, n=16384) and HBM GB/s vs 8 TB/s",
+            "metric": METRIC,
             "value": value, "unit": "SSSP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
