@@ -229,10 +229,8 @@ static int n_bucket(int32_t n) {
 }
 
 static int heuristic_cluster_size(int32_t max_pitch) {
-  // wide enough slices for long row segments, small enough to keep many solves in flight
-  if (max_pitch >= 8192) return 8;
-  if (max_pitch >= 2048) return 4;
-  return 2;
+  // slices of about 1024 columns: long row segments copied wide, yet many solves in flight
+  return std::min(16, std::max(2, max_pitch / 1024));
 }
 
 static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, int32_t k, int32_t* const* dist,
