@@ -230,7 +230,9 @@ static int n_bucket(int32_t n) {
 
 static int heuristic_cluster_size(int32_t max_pitch) {
   // slices of about 1024 columns: long row segments copied wide, yet many solves in flight
-  return std::min(16, std::max(2, max_pitch / 1024));
+  int c = 2;
+  while (c < 16 && c * 1024 < max_pitch) c *= 2;  // a power of two
+  return c;
 }
 
 static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, int32_t k, int32_t* const* dist,

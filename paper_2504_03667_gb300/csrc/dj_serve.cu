@@ -50,7 +50,11 @@ struct Slot {
 // Slices of about 1024 columns: wide ring copies, and clusters small enough to keep
 // many requests in flight (measured on the 64-graph serving mix: cluster size 16
 // for the n=16384 graphs raised saturation by 10 % and cut p99 by 15 % against 8).
-int heuristic_cluster(int32_t pitch) { return std::min(16, std::max(2, pitch / 1024)); }
+int heuristic_cluster(int32_t pitch) {
+  int c = 2;
+  while (c < 16 && c * 1024 < pitch) c *= 2;  // a power of two: slices of at most ~1024 columns
+  return c;
+}
 
 }  // namespace
 
