@@ -168,8 +168,8 @@ typedef struct dj_solve_opts {
                              whole rows, each CTA a share of them, and merges the per-column bests
                              through global memory around one more grid barrier (reading a whole
                              row per CTA streams HBM faster than every CTA reading its slice of
-                             every row).  0 = auto (2048 on graphs with at least n^2/32 finite
-                             entries, never on sparser ones), -1 = never. */
+                             every row).  0 = auto (n/8 clamped to 512..2048, on graphs with at
+                             least n^2/32 finite entries; never on sparser ones), -1 = never. */
   int32_t reserved[3];
 } dj_solve_opts;
 

@@ -556,7 +556,12 @@ namespace {
 
 constexpr int kRowsPerStage = 8;  // U: rows per ring stage
 constexpr int kGridListCap = 8192;  // grid engine: staged settled rows per segment
-constexpr int kRowSplitMin = 2048;  // grid engine: row-split phases from this many candidates on
+// Grid engine: a phase takes the row split once n / 8 nodes are its candidates, within
+// [512, 2048]: the split saves time in proportion to rows x row bytes and costs a fixed
+// barrier and merge, so smaller graphs profit from smaller phases (measured on GB300, p = 0.5:
+// n = 4096 fastest near 512, n = 8192 near 700..1100, n = 16384 flat from 1100 to 2048, and
+// p = 0.1 at n = 16384 slower below 2048).
+int auto_rowsplit_min(int32_t n) { return std::min(2048, std::max(512, static_cast<int>(n / 8))); }
 
 constexpr int kGridThreads = 512;
 constexpr int kClusterThreads = 256;
@@ -705,7 +710,7 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   // staged list, and slices below 2^16 columns (packed counts in the partials)
   const int rs_min = (!want_rs || L.rs_bytes == 0 || L.swcap > L.list_cap || L.swcap >= 65536) ? 0
                      : o.rowsplit > 0                                                         ? o.rowsplit
-                                                                                              : kRowSplitMin;
+                                                                                              : auto_rowsplit_min(g->n);
   const size_t snap_bytes = rs_min > 0 ? static_cast<size_t>(g->pitch) * 4 : 0;  // pitch is a multiple of 4
   const size_t gkey_bytes = rs_min > 0 ? static_cast<size_t>(2) * g->pitch * 8 : 0;
   uint8_t* ws = nullptr;
