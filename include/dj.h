@@ -136,7 +136,7 @@ int dj_graph_free(dj_graph* g);
                            visit order in one fused relaxation pass (same dist and pred) */
 #define DJ_MODE_PLAIN 2 /* literal Algorithm 1: one argmin + one row relaxation per step */
 
-#define DJ_ENGINE_AUTO 0
+#define DJ_ENGINE_AUTO 0     /* grid for n >= 4096, or n >= 2560 with at least n^2/4 finite entries */
 #define DJ_ENGINE_GRID 1    /* one cooperative persistent kernel over every SM; column slices per CTA */
 #define DJ_ENGINE_CLUSTER 2 /* one thread-block cluster; state in distributed shared memory */
 

@@ -93,8 +93,17 @@ extern "C" void dj_batch_opts_init(dj_batch_opts* o) {
 
 // ------------------------------------------------------------------ single solves
 
-// Size below which one cluster beats the whole-GPU grid engine (fewer, cheaper barriers).
+// Size below which one cluster beats the whole-GPU grid engine (fewer, cheaper barriers), and
+// the lower one for graphs with at least n^2/4 finite entries, whose few phases each move much
+// of the matrix (GB300, single solves, w 1..1000: p = 0.5 grid 134 / cluster 214 us at n = 3072,
+// 148 / 138 at n = 2048; p = 0.05 grid 459 / cluster 433 at n = 3072, 431 / 463 at n = 4096).
 static constexpr int32_t kGridMinN = 4096;
+static constexpr int32_t kGridMinNDense = 2560;
+
+static bool auto_grid(const dj_graph* g) {
+  const uint64_t n = static_cast<uint64_t>(g->n);
+  return g->n >= kGridMinN || (g->n >= kGridMinNDense && g->entries * 4 >= n * n);
+}
 
 static int default_cluster_size(int32_t n) {
   (void)n;
@@ -139,7 +148,7 @@ extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int3
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (g->format == DJ_FORMAT_CSR) return launch_csr(g, source, dist, pred, o, st);
   int engine = o.engine;
-  if (engine == DJ_ENGINE_AUTO) engine = g->n >= kGridMinN ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;
+  if (engine == DJ_ENGINE_AUTO) engine = auto_grid(g) ? DJ_ENGINE_GRID : DJ_ENGINE_CLUSTER;
   if (engine == DJ_ENGINE_GRID) return launch_grid(g, source, dist, pred, o, st);
   if (engine == DJ_ENGINE_CLUSTER) return solve_cluster_single(g, source, dist, pred, o, st);
   return set_error(DJ_EINVAL, "unknown engine");
