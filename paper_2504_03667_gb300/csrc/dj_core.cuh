@@ -547,6 +547,69 @@ __device__ __forceinline__ int stage_settled(const Get& get, int begin, int end,
   return static_cast<int>(sc->cnt[31]);
 }
 
+// stage_settled for the grid's published candidate lists, read by bulk copies:
+// candidates [begin, end) (entry i lies in region r with off[r] <= i <
+// off[r + 1], at cl + r * swcap + i - off[r]) come into `buf` in chunks of
+// buf_bytes / 16 entries, one copy per overlapping region (issued by thread r),
+// all completing on one mbarrier of the pair rbar (gt counts their phases,
+// the same in every thread); then the chunk is filtered from shared memory.
+// Sets ok = false if a chunk did not arrive in time.  Returns the count; ends
+// synced.
+__device__ __forceinline__ int stage_settled_bulk(const uint32_t* off, int G, const uint4* cl, int swcap, int begin,
+                                                  int end, const Decision& D, uint32_t bits_u, uint32_t* list,
+                                                  uint8_t* buf, uint32_t buf_bytes, uint64_t* rbar, uint32_t& gt,
+                                                  int64_t timeout_ns, BlockScratch* sc, bool& ok) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) sc->cnt[31] = 0;
+  const int per = static_cast<int>(buf_bytes / 16);
+  const uint4* b4 = reinterpret_cast<const uint4*>(buf);
+  for (int c0 = begin; c0 < end; c0 += per) {
+    const int c1 = min(end, c0 + per);
+    const uint32_t g = gt++;
+    uint64_t* bar = rbar + (g & 1u);
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(c1 - c0) * 16u);
+    __syncthreads();  // the expectation precedes the copies; earlier reads of buf are done
+    for (int r = threadIdx.x; r < G; r += blockDim.x) {
+      const int lo = max(static_cast<int>(off[r]), c0), hi = min(static_cast<int>(off[r + 1]), c1);
+      if (hi > lo) {
+        fence_proxy_async_smem();  // earlier generic accesses of buf precede the copy
+        bulk_g2s(buf + static_cast<size_t>(lo - c0) * 16, cl + static_cast<size_t>(r) * swcap + (lo - static_cast<int>(off[r])),
+                 static_cast<uint32_t>(hi - lo) * 16u, bar);
+      }
+    }
+    if (!mbar_wait_bounded(bar, (g >> 1) & 1u, timeout_ns)) {
+      ok = false;
+      mbar_wait_bounded(bar, (g >> 1) & 1u, timeout_ns);  // drain once more
+    }
+    constexpr int K = 4;
+    for (int i0 = 0; i0 < c1 - c0; i0 += K * static_cast<int>(blockDim.x)) {
+      uint4 e[K];
+      uint32_t bal[K], tot = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int i = i0 + k * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+        e[k] = i < c1 - c0 ? b4[i] : make_uint4(0xffffffffu, kInf, kInf, 0u);
+        bal[k] = __ballot_sync(0xffffffffu, e[k].x != 0xffffffffu && in_settled(e[k].x, e[k].y, e[k].z, D));
+        tot += __popc(bal[k]);
+      }
+      if (tot) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(&sc->cnt[31], tot);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if ((bal[k] >> lane) & 1u) list[pos + __popc(bal[k] & lt)] = ((e[k].y - D.m) << bits_u) | e[k].x;
+          pos += __popc(bal[k]);
+        }
+      }
+    }
+    fence_proxy_async_smem();  // this thread's reads of buf precede the next copies into it
+  }
+  __syncthreads();
+  return static_cast<int>(sc->cnt[31]);
+}
+
 // Entry i of a staged list, in the candidate form the relaxation takes.
 __device__ __forceinline__ uint4 staged_entry(const uint32_t* list, int i, const Decision& D, uint32_t bits_u) {
   const uint32_t tb = list[i];
@@ -670,8 +733,9 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
 }
 
 // Relax only the live groups glist[0, nlg) of this slice: the settled rows
-// among `total` candidates get(i) are staged into `list` (list_cap at a time)
-// and cut into chunks of kGatherChunk rows; work item (chunk c, group g) goes
+// among `total` candidates are staged into `list` (list_cap at a time, by
+// stage(begin, end), which returns their count and ends synced) and cut into
+// chunks of kGatherChunk rows; work item (chunk c, group g) goes
 // to thread (c * nlg + g) mod blockDim, so a group that needs every row is
 // spread over the whole block.  An item loads the group's 16 bytes of each of
 // its rows whose tie word is below the group's threshold gthr[g] (all of them
@@ -680,16 +744,15 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
 // atomicMin).  On entry bkey[j] must hold (dist[j] << 32) | ~0 for every
 // column.  Ends synced.
 constexpr int kGatherChunk = 16;
-template <class Get>
-__device__ __forceinline__ void relax_gather(const Get& get, int total, const Slice& s,
+template <class Stage>
+__device__ __forceinline__ void relax_gather(const Stage& stage, int total, const Slice& s,
                                              const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
                                              uint32_t bits_u, const uint32_t* glist, const uint64_t* gthr,
-                                             int nlg, uint32_t* list, int list_cap, uint64_t* bkey,
-                                             BlockScratch* sc) {
+                                             int nlg, uint32_t* list, int list_cap, uint64_t* bkey) {
   const uint32_t umask = (1u << bits_u) - 1u;
   constexpr int K = kGatherChunk;
   for (int seg = 0; seg < total; seg += list_cap) {
-    const int cnt = stage_settled(get, seg, min(total, seg + list_cap), D, bits_u, list, sc);
+    const int cnt = stage(seg, min(total, seg + list_cap));  // settled rows of [seg, ...) into list; synced
     const int items = nlg * ((cnt + kGatherChunk - 1) / kGatherChunk);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int c = it / nlg, g = it - c * nlg;

@@ -271,11 +271,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     } else if (nlg <= p.gather_max) {
       if (nlg > 0) {
         for (int j = threadIdx.x; j < s.sw; j += blockDim.x) bkey[j] = (static_cast<uint64_t>(s.dist[j]) << 32) | 0xFFFFFFFFu;
-        if (p.plain)
-          relax_gather([one](int) { return one; }, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list,
-                       p.list_cap, bkey, &sc);
-        else
-          relax_gather(get, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey, &sc);
+        if (p.plain) {
+          auto stage = [&](int b0, int b1) {
+            return stage_settled([one](int) { return one; }, b0, b1, D, p.bits_u, list, &sc);
+          };
+          relax_gather(stage, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey);
+        } else {
+          // the published lists come in by bulk copies through the (idle) ring region
+          bool ok = true;
+          auto stage = [&](int b0, int b1) {
+            return stage_settled_bulk(s_off, G, cl, swcap, b0, b1, D, p.bits_u, list, rings,
+                                      static_cast<uint32_t>(p.ring_bytes), rbar, rs_gt, p.timeout_ns, &sc, ok);
+          };
+          relax_gather(stage, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey);
+          if (!ok) {
+            atomicOr(p.words, kErrTimeout);
+            atomicExch(abort_flag, 1u);
+          }
+        }
       }
       if (tr && threadIdx.x == 0) tr[5] = global_ns();
       // 5. mark, commit, and the next partial
