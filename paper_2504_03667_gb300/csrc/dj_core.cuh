@@ -743,16 +743,176 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
 // into bkey (64-bit keys (candidate << 32) | tie word, shared-memory
 // atomicMin).  On entry bkey[j] must hold (dist[j] << 32) | ~0 for every
 // column.  Ends synced.
+// With the whole list in one segment, a column pass (gather_column_pass,
+// scratch in `bm`) first decides the columns that can only take a tie at the
+// IN bound from their tie sources and, on a symmetric matrix (sym), the
+// columns any row may improve from their own row; groups left with no other
+// live column drop out of the gather.
 constexpr int kGatherChunk = 16;
+
+// Tie sources of the columns: src[v * cap + k], k < cnt[v], are the u != v
+// with G[u][v] == minin[v] (cnt[v] > cap: too many to list).
+struct TieSources {
+  const int32_t* src;
+  const int32_t* cnt;
+  int32_t cap;  // 0: none
+};
+
+// Column pass of the gather path, before its row items.  `tab` (pitch 16-bit
+// entries, in shared memory) holds dist[u] - m for the settled rows of the
+// phase (0xFFFF: not settled); it is exact unless `exact` is false (some
+// settled row lies 0xFFFF or more above m).  Two kinds of live column leave
+// the group gather:
+//   - A column whose stored dist equals its bound m + minin[v] (>= L) can
+//     only take a tie, and only from a settled u with dist[u] = m and G[u][v]
+//     = minin[v]: every settled u has dist[u] >= m, and G[u][v] >= minin[v]
+//     off the diagonal (v's own zero diagonal offers v its dist with a tie
+//     word above the stored one, so it never commits).  Such a u is one of
+//     v's tie sources, and among those with dist[u] = m the smallest index has
+//     the smallest tie word.  One warp per column checks its listed sources.
+//   - On a symmetric matrix, a column any settled row may improve (dist above
+//     its bound) reads row v whole -- it is column v -- once, coalesced,
+//     against the table, instead of one 16-byte piece per settled row.
+// The groups' row thresholds are recomputed from their remaining columns and
+// glist / gthr compacted.  clist (2 * sw entries of shared memory) holds the
+// two column lists.  Returns the new group count; ends synced.
+__device__ __forceinline__ int gather_column_pass(const Slice& s, const int32_t* __restrict__ W, int64_t pitch,
+                                                  const Decision& D, uint32_t bits_u, const TieSources& ts,
+                                                  bool rows_ok, const uint16_t* tab, uint32_t* clist,
+                                                  uint32_t* glist, uint64_t* gthr, int nlg, uint64_t* bkey,
+                                                  BlockScratch* sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = static_cast<int>(blockDim.x >> 5);
+  uint32_t* tl = clist;          // tie-source columns
+  uint32_t* rl = clist + s.sw;   // whole-row columns
+  if (threadIdx.x == 0) {
+    sc->cnt[28] = 0;
+    sc->cnt[29] = 0;
+  }
+  __syncthreads();
+  for (int gi = threadIdx.x; gi < nlg; gi += blockDim.x) {
+    const int jv = static_cast<int>(glist[gi]);
+    uint64_t thr = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = 4 * jv + q;
+      const uint64_t t = column_live(s, col, D, bits_u);
+      if (t == 0) continue;
+      const uint32_t d = s.dist[col];
+      if (ts.cap > 0 && t < (1ull << 32) && D.use_in && d < kInf && d == D.m + s.minin[col]) {
+        tl[atomicAdd(&sc->cnt[28], 1u)] = static_cast<uint32_t>(col);
+        continue;
+      }
+      if (rows_ok && t == (1ull << 32)) {
+        rl[atomicAdd(&sc->cnt[29], 1u)] = static_cast<uint32_t>(col);
+        continue;
+      }
+      thr = t > thr ? t : thr;
+    }
+    gthr[gi] = thr;
+  }
+  __syncthreads();
+  const int ntl = static_cast<int>(sc->cnt[28]), nrl = static_cast<int>(sc->cnt[29]);
+  // tie-source columns, one warp each (a column with more sources than listed keeps its group)
+  for (int k = warp; k < ntl; k += nwarps) {
+    const int col = static_cast<int>(tl[k]);
+    const int v = s.c0 + col;
+    const int nsrc = ts.cnt[v];
+    uint32_t best = 0xFFFFFFFFu;
+    if (nsrc <= ts.cap && lane < nsrc) {
+      const uint32_t u = static_cast<uint32_t>(ts.src[static_cast<int64_t>(v) * ts.cap + lane]);
+      if (tab[u] == 0) best = u;
+    }
+    best = warp_min_u32(best);
+    if (nsrc > ts.cap) {  // back to the gather: fold the column's threshold into its group
+      if (lane == 0) {
+        const uint64_t t = column_live(s, col, D, bits_u);
+        for (int gi = 0; gi < nlg; ++gi)
+          if (static_cast<int>(glist[gi]) == col / 4) {
+            atomicMax(reinterpret_cast<unsigned long long*>(gthr + gi), static_cast<unsigned long long>(t));
+            break;
+          }
+      }
+    } else if (lane == 0 && best != 0xFFFFFFFFu) {
+      const uint64_t key = (static_cast<uint64_t>(s.dist[col]) << 32) | best;  // tie word (0 << bits) | u
+      atomicMin(reinterpret_cast<unsigned long long*>(bkey + col), static_cast<unsigned long long>(key));
+    }
+  }
+  // whole-row columns: the block reads row v (= column v) once, coalesced
+  const int nvec = static_cast<int>(pitch / 4);
+  const uint2* tab4 = reinterpret_cast<const uint2*>(tab);
+  for (int k = 0; k < nrl; ++k) {
+    const int col = static_cast<int>(rl[k]);
+    const int4* row = reinterpret_cast<const int4*>(W + static_cast<int64_t>(s.c0 + col) * pitch);
+    uint32_t bc = 0xFFFFFFFFu, bt = 0xFFFFFFFFu;
+    constexpr int R = 8;
+    for (int g0 = 0; g0 < nvec; g0 += R * static_cast<int>(blockDim.x)) {
+      int4 x[R];
+      uint2 t2[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int gv = g0 + r * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+        t2[r] = gv < nvec ? tab4[gv] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+        x[r] = (t2[r].x & t2[r].y) != 0xFFFFFFFFu ? __ldg(row + gv) : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int gv = g0 + r * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+        const uint32_t t4[4] = {t2[r].x & 0xFFFFu, t2[r].x >> 16, t2[r].y & 0xFFFFu, t2[r].y >> 16};
+        const uint32_t w4[4] = {static_cast<uint32_t>(x[r].x), static_cast<uint32_t>(x[r].y),
+                                static_cast<uint32_t>(x[r].z), static_cast<uint32_t>(x[r].w)};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (t4[q] != 0xFFFFu)
+            best_update(D.m + t4[q] + w4[q], (t4[q] << bits_u) | static_cast<uint32_t>(4 * gv + q), bc, bt);
+      }
+    }
+    const uint64_t key = warp_min_u64((static_cast<uint64_t>(bc) << 32) | bt);
+    if (lane == 0 && static_cast<uint32_t>(key) != 0xFFFFFFFFu)
+      atomicMin(reinterpret_cast<unsigned long long*>(bkey + col), static_cast<unsigned long long>(key));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int gi = 0; gi < nlg; ++gi)
+      if (gthr[gi]) {
+        glist[k] = glist[gi];
+        gthr[k] = gthr[gi];
+        ++k;
+      }
+    sc->cnt[28] = static_cast<uint32_t>(k);
+  }
+  __syncthreads();
+  return static_cast<int>(sc->cnt[28]);
+}
+
 template <class Stage>
 __device__ __forceinline__ void relax_gather(const Stage& stage, int total, const Slice& s,
                                              const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
-                                             uint32_t bits_u, const uint32_t* glist, const uint64_t* gthr,
-                                             int nlg, uint32_t* list, int list_cap, uint64_t* bkey) {
+                                             uint32_t bits_u, uint32_t* glist, uint64_t* gthr, int nlg,
+                                             uint32_t* list, int list_cap, uint64_t* bkey, const TieSources& ts,
+                                             bool sym, uint32_t* bm, int bm_words, BlockScratch* sc) {
   const uint32_t umask = (1u << bits_u) - 1u;
   constexpr int K = kGatherChunk;
   for (int seg = 0; seg < total; seg += list_cap) {
     const int cnt = stage(seg, min(total, seg + list_cap));  // settled rows of [seg, ...) into list; synced
+    // the column pass: whole list in one segment, and room for the table (2 bytes per column)
+    // plus two column lists in the scratch words
+    if ((ts.cap > 0 || sym) && total <= list_cap && bm_words >= static_cast<int>(pitch / 2 + 2 * s.sw)) {
+      uint16_t* tab = reinterpret_cast<uint16_t*>(bm);
+      if (threadIdx.x == 0) sc->cnt[27] = 0;
+      for (int i = threadIdx.x; i < static_cast<int>(pitch / 2); i += blockDim.x) bm[i] = 0xFFFFFFFFu;
+      __syncthreads();
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t tb = list[i];
+        const uint32_t dd = tb >> bits_u;
+        tab[tb & umask] = static_cast<uint16_t>(min(dd, 0xFFFEu));
+        if (dd >= 0xFFFEu) sc->cnt[27] = 1;  // the table is not exact
+      }
+      __syncthreads();
+      nlg = gather_column_pass(s, W, pitch, D, bits_u, ts, sym && sc->cnt[27] == 0, tab, bm + pitch / 2, glist, gthr,
+                               nlg, bkey, sc);
+      fence_proxy_async_smem();  // the scratch's generic accesses precede later copies into its bytes
+    }
     const int items = nlg * ((cnt + kGatherChunk - 1) / kGatherChunk);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int c = it / nlg, g = it - c * nlg;

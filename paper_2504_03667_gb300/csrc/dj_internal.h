@@ -18,6 +18,9 @@ struct dj_graph {
   int32_t* W = nullptr;       // n x pitch, row-major
   int32_t* minout = nullptr;  // n row minima (then the n column minima, same allocation)
   int32_t* minin = nullptr;   // n column minima
+  int32_t* tsrc = nullptr;    // n x tcap tie sources: the u != v with W[u][v] == minin[v]
+  int32_t* tcnt = nullptr;    // n counts (above tcap: not listed)
+  int32_t tcap = 0;
   uint64_t bytes = 0;
   uint64_t entries = 0;       // finite off-diagonal matrix entries (directed edges)
   int32_t format = DJ_FORMAT_DENSE;  // DJ_FORMAT_CSR: no matrix, the arrays below

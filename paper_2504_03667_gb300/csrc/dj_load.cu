@@ -112,6 +112,28 @@ __global__ void k_colmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   if (mn < kInf) atomicMin(minin + v, static_cast<int32_t>(mn));
 }
 
+// Tie sources: for every column v, the rows u != v with W[u][v] == minin[v]
+// (one warp per row, coalesced reads of the row and of minin), up to cap per
+// column; tcnt[v] counts them all (starts at 0).  A column whose stored dist
+// equals m + minin[v] can only be tied by one of these rows.
+constexpr int kTieSourceCap = 32;
+__global__ void k_tiesrc(const int32_t* __restrict__ W, int64_t pitch, int32_t n, const int32_t* __restrict__ minin,
+                         int32_t* __restrict__ tsrc, int32_t* __restrict__ tcnt, int32_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t* row = W + u * pitch;
+    for (int64_t v = lane; v < n; v += 32) {
+      const int32_t x = row[v];
+      if (v != u && static_cast<uint32_t>(x) < kInf && x == minin[v] && tcnt[v] <= cap) {
+        const int32_t pos = atomicAdd(tcnt + v, 1);
+        if (pos < cap) tsrc[v * cap + pos] = static_cast<int32_t>(u);
+      }
+    }
+  }
+}
+
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t value) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -167,21 +189,35 @@ static int alloc_graph(int32_t n, int directed, dj_graph** out) {
     return set_error(DJ_ENOMEM, "cudaMalloc of the row / column minima failed");
   }
   g->minin = g->minout + n;
-  g->bytes = mbytes + 2 * static_cast<size_t>(n) * sizeof(int32_t);
+  g->tcap = kTieSourceCap;
+  e = cudaMalloc(&g->tsrc, static_cast<size_t>(n) * (kTieSourceCap + 1) * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->W);
+    cudaFree(g->minout);
+    delete g;
+    return set_error(DJ_ENOMEM, "cudaMalloc of the tie sources failed");
+  }
+  g->tcnt = g->tsrc + static_cast<size_t>(n) * kTieSourceCap;
+  g->bytes = mbytes + static_cast<size_t>(n) * (kTieSourceCap + 3) * sizeof(int32_t);
   *out = g;
   return DJ_OK;
 }
 
-// Column minima: a copy of the row minima for undirected graphs, else k_colmin.
+// Column minima (a copy of the row minima for undirected graphs, else
+// k_colmin), then the columns' tie sources.
 static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
   k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
   if (!g->directed) {
     cudaMemcpyAsync(g->minin, g->minout, static_cast<size_t>(g->n) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    return;
+  } else {
+    k_fill_i32<<<grid_for(g->n), 256, 0, st>>>(g->minin, g->n, static_cast<int32_t>(kInf));
+    dim3 grid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
+    k_colmin<<<grid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin);
   }
-  k_fill_i32<<<grid_for(g->n), 256, 0, st>>>(g->minin, g->n, static_cast<int32_t>(kInf));
-  dim3 grid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
-  k_colmin<<<grid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin);
+  cudaMemsetAsync(g->tcnt, 0, static_cast<size_t>(g->n) * sizeof(int32_t), st);
+  k_tiesrc<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc,
+                                                                       g->tcnt, g->tcap);
 }
 
 // Row and column minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
@@ -372,6 +408,7 @@ extern "C" int dj_graph_free(dj_graph* g) {
   if (!g) return DJ_OK;
   cudaFree(g->W);
   cudaFree(g->minout);  // minin shares this allocation
+  cudaFree(g->tsrc);    // tcnt shares this allocation
   cudaFree(g->row_ptr);
   cudaFree(g->col);
   cudaFree(g->wt);

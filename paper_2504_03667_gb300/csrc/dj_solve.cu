@@ -62,6 +62,8 @@ struct GridParams {
   int32_t ring_bytes;  // bytes of the ring region (also the row-split buffers)
   uint32_t* gsnap;     // [pitch] column snapshots at the start of a row-split phase
   unsigned long long* gkey;  // [2][pitch] merged row-split keys per phase parity, all ones between uses
+  TieSources ts;       // the columns' tie sources (cap 0: not used)
+  int32_t sym;         // the matrix is symmetric (undirected graph): column v is row v
 };
 
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
@@ -275,7 +277,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
           auto stage = [&](int b0, int b1) {
             return stage_settled([one](int) { return one; }, b0, b1, D, p.bits_u, list, &sc);
           };
-          relax_gather(stage, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey);
+          relax_gather(stage, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey,
+                       TieSources{nullptr, nullptr, 0}, false, nullptr, 0, &sc);
         } else {
           // the published lists come in by bulk copies through the (idle) ring region
           bool ok = true;
@@ -283,7 +286,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
             return stage_settled_bulk(s_off, G, cl, swcap, b0, b1, D, p.bits_u, list, rings,
                                       static_cast<uint32_t>(p.ring_bytes), rbar, rs_gt, p.timeout_ns, &sc, ok);
           };
-          relax_gather(stage, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey);
+          relax_gather(stage, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey, p.ts,
+                       p.sym != 0, reinterpret_cast<uint32_t*>(rings), p.ring_bytes / 4, &sc);
           if (!ok) {
             atomicOr(p.words, kErrTimeout);
             atomicExch(abort_flag, 1u);
@@ -768,6 +772,8 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.gsnap = rs_min > 0 ? reinterpret_cast<uint32_t*>(ws + ctl_bytes + part_bytes + cand_bytes) : nullptr;
   p.gkey = rs_min > 0 ? reinterpret_cast<unsigned long long*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes)
                       : nullptr;
+  p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
+  p.sym = g->directed ? 0 : 1;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   cudaFreeAsync(ws, st);
@@ -1088,6 +1094,8 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.ring_bytes = static_cast<int32_t>(ring_region(L, nwarps));
   p.gsnap = nullptr;
   p.gkey = nullptr;
+  p.ts = p.use_in && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
+  p.sym = g->directed ? 0 : 1;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");

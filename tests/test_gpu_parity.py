@@ -166,12 +166,17 @@ def test_relaxation_paths(dj, orc, live, rowsplit):
     slice with no live column, load only the live groups when few, row split for big phases),
     loading only the live groups in every phase (gather), and row split in every phase all give
     Algorithm 1's dist and pred.  Dense graphs with weights 1..3 make ties on both dist and pred
-    pervasive; zero weights turn the IN bound off."""
+    pervasive; zero weights turn the IN bound off; narrow weight ranges give columns a few
+    dozen rows of their minimum in-weight, the tie sources the gather path settles tie-only
+    columns from."""
     cases = [
         ("dense ties", graphgen.bernoulli(4096, 0.5, 1, 3, seed=91), (0, 1, 2)),
         ("directed ties", graphgen.random_edges(5003, 6 * 5003, 1, 3, seed=92, directed=True), (0, 1)),
         ("zero weights", graphgen.random_edges(4099, 5 * 4099, 0, 2, seed=93, directed=False), (0, 1)),
         ("sparse wide weights", graphgen.bernoulli(6000, 0.01, 1, 1000, seed=94), (0, 1)),
+        # ~22 rows of weight 1 into each column: most columns list their tie sources, some overflow
+        ("tie sources", graphgen.bernoulli(3000, 0.3, 1, 40, seed=96), (0, 1)),
+        ("directed tie sources", graphgen.random_edges(4000, 40 * 4000, 1, 20, seed=97, directed=True), (0, 1)),
     ]
     for what, e, modes in cases:
         G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
