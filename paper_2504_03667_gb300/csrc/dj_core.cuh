@@ -484,21 +484,44 @@ __device__ __forceinline__ uint64_t column_live(const Slice& s, int j, const Dec
 // The 4-column groups of this slice that hold a live column, into glist (any
 // order), with the group's row threshold (the largest of its columns') in
 // gthr.  Returns their count; ends synced.
+// Also counts, for the choice of path, the groups the gather's column pass
+// would leave to row items (sc->cnt[26]: a live column that is neither a
+// tie-only column at m + minin[v] (with tie sources, `ties`) nor, on a
+// symmetric matrix (`rows`), one any row may improve) and those improvable
+// columns (sc->cnt[25]; beyond the pass's kMaxRowColumns their groups are
+// gathered too).
 __device__ __forceinline__ int live_groups(const Slice& s, const Decision& D, uint32_t bits_u, uint32_t* glist,
-                                           uint64_t* gthr, BlockScratch* sc) {
-  if (threadIdx.x == 0) sc->cnt[30] = 0;
+                                           uint64_t* gthr, BlockScratch* sc, bool ties = false, bool rows = false) {
+  if (threadIdx.x == 0) {
+    sc->cnt[30] = 0;
+    sc->cnt[26] = 0;
+    sc->cnt[25] = 0;
+  }
   __syncthreads();
   for (int jv = threadIdx.x; jv < s.nvec; jv += blockDim.x) {
-    uint64_t thr = column_live(s, 4 * jv, D, bits_u);
+    uint64_t thr = 0;
+    bool hard = false;
+    uint32_t nimp = 0;
 #pragma unroll
-    for (int c = 1; c < 4; ++c) {
-      const uint64_t t = column_live(s, 4 * jv + c, D, bits_u);
+    for (int c = 0; c < 4; ++c) {
+      const int col = 4 * jv + c;
+      const uint64_t t = column_live(s, col, D, bits_u);
       thr = t > thr ? t : thr;
+      if (t == 0) continue;
+      const uint32_t d = s.dist[col];
+      if (ties && t < (1ull << 32) && d < kInf && d == D.m + s.minin[col]) continue;
+      if (rows && t == (1ull << 32)) {
+        ++nimp;
+        continue;
+      }
+      hard = true;
     }
     if (thr) {
       const uint32_t i = atomicAdd(&sc->cnt[30], 1u);
       glist[i] = static_cast<uint32_t>(jv);
       gthr[i] = thr;
+      if (hard) atomicAdd(&sc->cnt[26], 1u);
+      if (nimp) atomicAdd(&sc->cnt[25], nimp);
     }
   }
   __syncthreads();
@@ -749,6 +772,7 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
 // columns any row may improve from their own row; groups left with no other
 // live column drop out of the gather.
 constexpr int kGatherChunk = 16;
+constexpr int kMaxRowColumns = 4;  // whole-row reads of the gather's column pass per CTA (one after another)
 
 // Tie sources of the columns: src[v * cap + k], k < cnt[v], are the u != v
 // with G[u][v] == minin[v] (cnt[v] > cap: too many to list).
@@ -803,15 +827,18 @@ __device__ __forceinline__ int gather_column_pass(const Slice& s, const int32_t*
         continue;
       }
       if (rows_ok && t == (1ull << 32)) {
-        rl[atomicAdd(&sc->cnt[29], 1u)] = static_cast<uint32_t>(col);
-        continue;
+        const uint32_t k = atomicAdd(&sc->cnt[29], 1u);
+        if (k < static_cast<uint32_t>(kMaxRowColumns)) {  // at most this many rows; the rest stay gathered
+          rl[k] = static_cast<uint32_t>(col);
+          continue;
+        }
       }
       thr = t > thr ? t : thr;
     }
     gthr[gi] = thr;
   }
   __syncthreads();
-  const int ntl = static_cast<int>(sc->cnt[28]), nrl = static_cast<int>(sc->cnt[29]);
+  const int ntl = static_cast<int>(sc->cnt[28]), nrl = min(static_cast<int>(sc->cnt[29]), kMaxRowColumns);
   // tie-source columns, one warp each (a column with more sources than listed keeps its group)
   for (int k = warp; k < ntl; k += nwarps) {
     const int col = static_cast<int>(tl[k]);

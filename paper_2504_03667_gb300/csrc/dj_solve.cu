@@ -245,7 +245,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     // row split for a big phase after which a fair share of the nodes stays unsettled (otherwise
     // few columns are live and the filtered paths read less); the same decision in every CTA
     const bool rowsplit = p.rs_min > 0 && !p.plain && total >= p.rs_min && 16ull * s_rem >= static_cast<uint64_t>(p.n);
-    const int nlg = rowsplit ? 0 : p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc) : s.nvec;
+    // the gather's column pass applies: the whole list in one segment, room for its table and lists
+    const bool colpass = !p.plain && (p.ts.cap > 0 || p.sym) && total <= p.list_cap &&
+                         p.ring_bytes / 4 >= static_cast<int>(p.pitch / 2) + 2 * s.sw;
+    const int nlg = rowsplit           ? 0
+                    : p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc, colpass && p.ts.cap > 0,
+                                                      colpass && p.sym != 0)
+                                        : s.nvec;
+    // gather when few groups are live, or when the column pass leaves few to row items and few
+    // whole rows to read
+    const bool gather =
+        p.gather_max >= 0 &&
+        (nlg <= p.gather_max ||
+         (colpass && static_cast<int>(sc.cnt[26]) + max(0, static_cast<int>(sc.cnt[25]) - kMaxRowColumns) <= p.gather_max));
     if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(rowsplit ? 0xFFFFu : nlg) << 32;
     if (rowsplit) {
       unsigned long long* gk = p.gkey + static_cast<size_t>(phase & 1) * p.pitch;
@@ -270,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       __syncthreads();
       if (tr && threadIdx.x == 0) tr[5] = global_ns();
       commit_keys(s, D, p.bits_u, bkey, part);
-    } else if (nlg <= p.gather_max) {
+    } else if (gather) {
       if (nlg > 0) {
         for (int j = threadIdx.x; j < s.sw; j += blockDim.x) bkey[j] = (static_cast<uint64_t>(s.dist[j]) << 32) | 0xFFFFFFFFu;
         if (p.plain) {
