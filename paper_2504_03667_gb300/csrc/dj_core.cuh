@@ -498,6 +498,23 @@ __device__ __forceinline__ int live_groups(const Slice& s, const Decision& D, ui
     sc->cnt[25] = 0;
   }
   __syncthreads();
+  if (!ties && !rows) {  // no column pass: only the groups and their thresholds
+    for (int jv = threadIdx.x; jv < s.nvec; jv += blockDim.x) {
+      uint64_t thr = column_live(s, 4 * jv, D, bits_u);
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
+        const uint64_t t = column_live(s, 4 * jv + c, D, bits_u);
+        thr = t > thr ? t : thr;
+      }
+      if (thr) {
+        const uint32_t i = atomicAdd(&sc->cnt[30], 1u);
+        glist[i] = static_cast<uint32_t>(jv);
+        gthr[i] = thr;
+      }
+    }
+    __syncthreads();
+    return static_cast<int>(sc->cnt[30]);
+  }
   for (int jv = threadIdx.x; jv < s.nvec; jv += blockDim.x) {
     uint64_t thr = 0;
     bool hard = false;
@@ -766,9 +783,9 @@ __device__ __forceinline__ bool relax_pull(const Get& get, int total, const Slic
 // into bkey (64-bit keys (candidate << 32) | tie word, shared-memory
 // atomicMin).  On entry bkey[j] must hold (dist[j] << 32) | ~0 for every
 // column.  Ends synced.
-// With the whole list in one segment, a column pass (gather_column_pass,
-// scratch in `bm`) first decides the columns that can only take a tie at the
-// IN bound from their tie sources and, on a symmetric matrix (sym), the
+// With `colpass` (the whole list in one segment, room in `bm`), a column pass
+// (gather_column_pass) first decides the columns that can only take a tie at
+// the IN bound from their tie sources and, on a symmetric matrix (sym), the
 // columns any row may improve from their own row; groups left with no other
 // live column drop out of the gather.
 constexpr int kGatherChunk = 16;
@@ -917,14 +934,14 @@ __device__ __forceinline__ void relax_gather(const Stage& stage, int total, cons
                                              const int32_t* __restrict__ W, int64_t pitch, const Decision& D,
                                              uint32_t bits_u, uint32_t* glist, uint64_t* gthr, int nlg,
                                              uint32_t* list, int list_cap, uint64_t* bkey, const TieSources& ts,
-                                             bool sym, uint32_t* bm, int bm_words, BlockScratch* sc) {
+                                             bool sym, bool colpass, uint32_t* bm, BlockScratch* sc) {
   const uint32_t umask = (1u << bits_u) - 1u;
   constexpr int K = kGatherChunk;
   for (int seg = 0; seg < total; seg += list_cap) {
     const int cnt = stage(seg, min(total, seg + list_cap));  // settled rows of [seg, ...) into list; synced
-    // the column pass: whole list in one segment, and room for the table (2 bytes per column)
-    // plus two column lists in the scratch words
-    if ((ts.cap > 0 || sym) && total <= list_cap && bm_words >= static_cast<int>(pitch / 2 + 2 * s.sw)) {
+    // the column pass (the caller checked that it applies: the whole list in one segment, room in
+    // bm for the table (2 bytes per column) plus two column lists)
+    if (colpass) {
       uint16_t* tab = reinterpret_cast<uint16_t*>(bm);
       if (threadIdx.x == 0) sc->cnt[27] = 0;
       for (int i = threadIdx.x; i < static_cast<int>(pitch / 2); i += blockDim.x) bm[i] = 0xFFFFFFFFu;

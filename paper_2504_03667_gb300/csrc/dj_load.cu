@@ -112,24 +112,25 @@ __global__ void k_colmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   if (mn < kInf) atomicMin(minin + v, static_cast<int32_t>(mn));
 }
 
-// Tie sources: for every column v, the rows u != v with W[u][v] == minin[v]
-// (one warp per row, coalesced reads of the row and of minin), up to cap per
-// column; tcnt[v] counts them all (starts at 0).  A column whose stored dist
-// equals m + minin[v] can only be tied by one of these rows.
+// Tie sources: for every column v, the rows u != v with W[u][v] == minin[v],
+// up to cap per column; tcnt[v] counts them all (starts at 0).  A column whose
+// stored dist equals m + minin[v] can only be tied by one of these rows.  A
+// block covers 256 columns x kColRows rows like k_colmin: each thread keeps
+// its column's minin in a register and reads the rows coalesced.
 constexpr int kTieSourceCap = 32;
 __global__ void k_tiesrc(const int32_t* __restrict__ W, int64_t pitch, int32_t n, const int32_t* __restrict__ minin,
                          int32_t* __restrict__ tsrc, int32_t* __restrict__ tcnt, int32_t cap) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t u = warp; u < n; u += nwarps) {
-    const int32_t* row = W + u * pitch;
-    for (int64_t v = lane; v < n; v += 32) {
-      const int32_t x = row[v];
-      if (v != u && static_cast<uint32_t>(x) < kInf && x == minin[v] && tcnt[v] <= cap) {
-        const int32_t pos = atomicAdd(tcnt + v, 1);
-        if (pos < cap) tsrc[v * cap + pos] = static_cast<int32_t>(u);
-      }
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kColRows;
+  if (v >= n) return;
+  const int32_t mv = minin[v];
+  if (static_cast<uint32_t>(mv) >= kInf) return;  // no finite weight into v
+  const int64_t r1 = min(static_cast<int64_t>(n), r0 + kColRows);
+#pragma unroll 8
+  for (int64_t u = r0; u < r1; ++u) {
+    if (W[u * pitch + v] == mv && u != v) {
+      const int32_t pos = atomicAdd(tcnt + v, 1);
+      if (pos < cap) tsrc[v * cap + pos] = static_cast<int32_t>(u);
     }
   }
 }
@@ -216,8 +217,8 @@ static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
     k_colmin<<<grid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin);
   }
   cudaMemsetAsync(g->tcnt, 0, static_cast<size_t>(g->n) * sizeof(int32_t), st);
-  k_tiesrc<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc,
-                                                                       g->tcnt, g->tcap);
+  dim3 tgrid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
+  k_tiesrc<<<tgrid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc, g->tcnt, g->tcap);
 }
 
 // Row and column minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.

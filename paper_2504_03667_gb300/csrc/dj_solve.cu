@@ -68,6 +68,7 @@ struct GridParams {
 
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
 constexpr int kRowSplitCpt = 8;          // row split: 4-column groups per thread per column chunk
+constexpr int kColPassMin = 1024;        // gather column pass: phases with at least this many candidates
 
 template <int V, int U, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
@@ -245,8 +246,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
     // row split for a big phase after which a fair share of the nodes stays unsettled (otherwise
     // few columns are live and the filtered paths read less); the same decision in every CTA
     const bool rowsplit = p.rs_min > 0 && !p.plain && total >= p.rs_min && 16ull * s_rem >= static_cast<uint64_t>(p.n);
-    // the gather's column pass applies: the whole list in one segment, room for its table and lists
-    const bool colpass = !p.plain && (p.ts.cap > 0 || p.sym) && total <= p.list_cap &&
+    // the gather's column pass: on undirected graphs (measured: it costs the sparse directed graph
+    // more than it saves), for phases with enough settled rows to pay for it, the whole list in one
+    // segment, room for its table and lists
+    const bool colpass = !p.plain && p.sym && total >= kColPassMin && total <= p.list_cap &&
                          p.ring_bytes / 4 >= static_cast<int>(p.pitch / 2) + 2 * s.sw;
     const int nlg = rowsplit           ? 0
                     : p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc, colpass && p.ts.cap > 0,
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
             return stage_settled([one](int) { return one; }, b0, b1, D, p.bits_u, list, &sc);
           };
           relax_gather(stage, 1, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey,
-                       TieSources{nullptr, nullptr, 0}, false, nullptr, 0, &sc);
+                       TieSources{nullptr, nullptr, 0}, false, false, nullptr, &sc);
         } else {
           // the published lists come in by bulk copies through the (idle) ring region
           bool ok = true;
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
                                       static_cast<uint32_t>(p.ring_bytes), rbar, rs_gt, p.timeout_ns, &sc, ok);
           };
           relax_gather(stage, total, s, p.W, p.pitch, D, p.bits_u, glist, gthr, nlg, list, p.list_cap, bkey, p.ts,
-                       p.sym != 0, reinterpret_cast<uint32_t*>(rings), p.ring_bytes / 4, &sc);
+                       p.sym != 0, colpass, reinterpret_cast<uint32_t*>(rings), &sc);
           if (!ok) {
             atomicOr(p.words, kErrTimeout);
             atomicExch(abort_flag, 1u);
