@@ -44,10 +44,6 @@
 //     A CTA whose slice has no such "live" column skips the relaxation; one
 //     with few live columns loads only their 16-byte groups, and only from
 //     the rows that can still win there (relax_gather).
-//   - A tie-only column at m + minin[v] can only be tied by a settled u with
-//     dist[u] = m and G[u][v] = minin[v] (one of v's tie sources, listed at
-//     load), and on an undirected graph column v is row v: the gather's
-//     column pass decides such columns without reading row pieces.
 // All sums are unsigned 32-bit: dist <= INF and G <= INF, so dist + G never
 // wraps, and an INF entry yields a candidate >= INF that never improves.
 #pragma once
