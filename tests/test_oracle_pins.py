@@ -31,7 +31,7 @@ def test_golden_solves(orc, fixture):
         assert np.array_equal(P.floyd_warshall(G)[s], dist.astype(np.int64))
 
 
-def test_north_star_example_distances(orc):
+def test_worked_example_distances_from_node_0(orc):
     g = P.parse_golden("worked_4node.txt")
     d, _ = orc.dijkstra(g["matrices"]["undirected"], 0)
     assert d.tolist() == [0, 2, 3, 5]
