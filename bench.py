@@ -79,6 +79,9 @@ class ClockSampler:
         self.marks.append(time.time())
 
     def stop(self) -> dict:
+        """Clocks over the window from the first mark (soak start) to the last (end of the timed
+        region): the soak and warm-up keep the GPU under the same load, so the window is long
+        enough for the 100 ms sampler even when the timed region itself lasts milliseconds."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.15)
@@ -108,7 +111,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(power) if power else None}
+                "window": "soak + warm-up + timed region (the same solve back to back)",
+                "window_s": round(t1 - t0, 3), "power_w_max": max(power) if power else None}
 
 
 def _dist_setup(n_gpus: int):
@@ -239,7 +243,9 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.25)  # the sampler's first lines
     # untimed soak so the clock sampler sees the GPU under this load
+    clocks.mark()
     t_soak = time.time()
     i = 0
     while time.time() - t_soak < args.soak_s:
@@ -254,7 +260,6 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    clocks.mark()
     e0.record(stream)
     for i in range(args.steps):
         step(i)
@@ -377,7 +382,9 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
     """e2e through host buffers, the batched workload and the plain one-launch-per-solve form."""
     out = {}
     n = e.n
-    # e2e: matrix host->device (pinned) + solve + dist/pred device->host, every step
+    # e2e: matrix host->device (pinned) + solve + dist/pred device->host, every step, timed with
+    # CUDA events on the solve stream (dj_sssp_host synchronises it, so host gaps are included)
+    numa = _numa_placement(torch)
     W_host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
     Wnp = dj.dj_graph_download(g)
     W_host.numpy()[:] = Wnp
@@ -387,14 +394,30 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
     for i in range(2):
         dj.dj_graph_upload(g, W_host, stream)
         dj.dj_sssp_host(g, int(srcs[i]), dh, ph, stream)
-    steps = 10
-    t0 = time.perf_counter()
+    steps = 20
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
     for i in range(steps):
         dj.dj_graph_upload(g, W_host, stream)
         dj.dj_sssp_host(g, int(srcs[i % 64]), dh, ph, stream)
-    el = time.perf_counter() - t0
+    a1.record(stream)
+    a1.synchronize()
+    el = a0.elapsed_time(a1) / 1e3
+    # the bare host->device copy of the same pinned matrix, for the link's share of a step
+    W_dev = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        W_dev.copy_(W_host, non_blocking=True)
+        a0.record(stream)
+        for _ in range(3):
+            W_dev.copy_(W_host, non_blocking=True)
+        a1.record(stream)
+    a1.synchronize()
+    copy_gbs = 3 * n * n * 4 / (a0.elapsed_time(a1) / 1e3) / 1e9
+    del W_dev
     out["e2e"] = {"value": steps / el, "unit": "SSSP/s", "h2d_bytes_per_step": n * n * 4,
-                  "d2h_bytes_per_step": 2 * n * 4, "steps": steps,
+                  "d2h_bytes_per_step": 2 * n * 4, "steps": steps, "timer": "CUDA events on the solve stream",
+                  "bare_h2d_copy_gbs": copy_gbs, "host_numa": numa,
                   "what": "dj_graph_upload (pinned host matrix) + dj_sssp_host (results to pinned host), per step"}
     del W_host
     # resident-graph e2e: only the source in and dist/pred out per step
@@ -418,6 +441,10 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
     el = time.perf_counter() - t0
     out["plain_form_n16384"] = {"value": reps / el, "unit": "SSSP/s",
                                 "what": "one node per step (Algorithm 1 literally), one launch per solve, synced"}
+    # the other single-solve workloads, each with its own roofline (n^2 * 4 bytes per solve)
+    out["dense_n1024_p0.1"] = single_workload(dj, torch, graphgen, "dense_n1024_p0.1", stream, 400)
+    out["sparse_directed_n32768_deg8"] = single_workload(dj, torch, graphgen, "sparse_directed_n32768_deg8",
+                                                         stream, 16)
     # the paper's own GPU formulation (label-correcting sweeps, Algorithms 3 and 4) rebuilt
     # coalesced, on the same workload: exact dist, a shortest-path-tree pred
     for i in range(3):
@@ -505,7 +532,8 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
                     "solves_per_batch": k, "autotune": tune,
                     "hbm_gbs_algorithmic": k * be.n * be.n * 4 / (batch_ms / 1e3) / 1e9,
                     "plain_form_value": plain_rate, "vs_plain_form": batch_rate / plain_rate,
-                    "phase_single_launch_value": single_rate, "vs_phase_single_launch": batch_rate / single_rate}
+                    "phase_single_launch_value": single_rate, "vs_phase_single_launch": batch_rate / single_rate,
+                    "cpu_baseline": batch_cpu_baseline(be, bs)}
     b.free()
     bg.free()
     out["serve"] = serving_measurement(dj, torch, graphgen, stream)
@@ -549,8 +577,24 @@ def serving_measurement(dj, torch, graphgen, stream) -> dict:
         dj.dj_sync(stream)
         t_plain += time.perf_counter() - t1
     plain_rate = len(sample) / t_plain
+    # the fast single-solve path on the same sample: one dj_sssp launch per request, synchronous
+    for r in sample[:2]:
+        g = graphs[int(tr.req_graph[r])]
+        d, p = bufs[int(dj.dj_graph_get_info(g)["n"])]
+        dj.dj_sssp(g, int(tr.req_source[r]), d, p, stream)
+    dj.dj_sync(stream)
+    t_single = 0.0
+    for r in sample:
+        g = graphs[int(tr.req_graph[r])]
+        d, p = bufs[int(dj.dj_graph_get_info(g)["n"])]
+        t1 = time.perf_counter()
+        dj.dj_sssp(g, int(tr.req_source[r]), d, p, stream)
+        dj.dj_sync(stream)
+        t_single += time.perf_counter() - t1
+    single_rate = len(sample) / t_single
     for g in graphs:
         g.free()
+    cpu = serve_cpu_baseline(graphgen, spec, tr)
     return {"workload": "serving_64graphs_10000req", "graphs": spec["graphs"], "requests": spec["requests"],
             "resident_bytes": resident, "setup_s": setup_s,
             "saturation_solves_per_s": sat["solves_per_s"],
@@ -558,7 +602,128 @@ def serving_measurement(dj, torch, graphgen, stream) -> dict:
             "p90_us": live["p90_us"], "p99_us": live["p99_us"], "max_us": live["max_us"],
             "deferred_requests": live["rejected"], "kernel_launches": live["kernel_launches"],
             "plain_form_value": plain_rate, "vs_plain_form": live["solves_per_s"] / plain_rate,
-            "plain_form_sample": f"{len(sample)} requests of the trace, one plain launch each, synchronous"}
+            "plain_form_sample": f"{len(sample)} requests of the trace, one plain launch each, synchronous",
+            "phase_single_launch_value": single_rate, "vs_phase_single_launch": live["solves_per_s"] / single_rate,
+            "phase_single_launch_sample": f"the same {len(sample)} requests, one dj_sssp launch each, synchronous",
+            "cpu_baseline": cpu}
+
+
+def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
+    """One of the single-source workloads: `reps` back-to-back dj_sssp solves (default engine and
+    mode, sources cycling through 16 seeded distinct nodes), timed with CUDA events on the solve
+    stream, and its roofline against n^2 * 4 algorithmic bytes per solve."""
+    spec = graphgen.WORKLOADS[name]
+    e = graphgen.make_graph(spec)
+    n = e.n
+    g = dj.dj_load_edges(n, e.src, e.dst, e.w, e.directed)
+    del e
+    srcs = [graphgen.workload_source(spec)] + [int(x) for x in graphgen.sources(n, 15, spec["seed"] + 100)]
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = torch.empty_like(d)
+    for i in range(5):
+        dj.dj_sssp(g, srcs[i % 16], d, p, stream)
+    dj.dj_sync(stream)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for i in range(reps):
+        dj.dj_sssp(g, srcs[i % 16], d, p, stream)
+    c1.record(stream)
+    dj.dj_sync(stream)
+    s_per = c0.elapsed_time(c1) / 1e3 / reps
+    # phases of one solve from the workload's own source (grid engine only reports them)
+    dj.dj_sssp(g, srcs[0], d, p, stream)
+    dj.dj_sync(stream)
+    phases = dj.dj_last_phases()
+    info = dj.dj_graph_get_info(g)
+    g.free()
+    peak, peak_kind = _peaks()
+    achieved = n * n * 4 / s_per / 1e9
+    return {"value": 1.0 / s_per, "unit": "SSSP/s", "us_per_solve": 1e6 * s_per, "solves_timed": reps,
+            "phases_first_source": phases if phases >= 0 else None,
+            "engine": "grid" if (n >= 4096 or (n >= 2560 and info["entries"] * 4 >= n * n)) else "cluster",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes_per_launch": n * n * 4,
+                         "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None},
+            "timer": "CUDA events over back-to-back dj_sssp calls (launch overhead included)"}
+
+
+def _numa_placement(torch) -> dict:
+    """NUMA node of the GPU (sysfs) and of the CPUs this process allocates pinned memory from."""
+    out = {"gpu_node": None, "process_nodes": None}
+    try:
+        q = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()), "--query-gpu=pci.bus_id",
+                            "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, rest = q.split(":", 1)  # nvidia-smi prints an 8-digit domain, sysfs a 4-digit one
+        bus = f"{int(dom, 16):04x}:{rest}".lower()
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+            out["gpu_node"] = int(f.read().strip())
+    except Exception:
+        pass
+    try:
+        cpus = os.sched_getaffinity(0)
+        nodes = set()
+        base = "/sys/devices/system/node"
+        for nd in os.listdir(base):
+            if not nd.startswith("node"):
+                continue
+            with open(os.path.join(base, nd, "cpulist")) as f:
+                spec = f.read().strip()
+            ids = set()
+            for part in spec.split(","):
+                if "-" in part:
+                    a, b = part.split("-")
+                    ids.update(range(int(a), int(b) + 1))
+                elif part:
+                    ids.add(int(part))
+            if ids & cpus:
+                nodes.add(int(nd[4:]))
+        out["process_nodes"] = sorted(nodes)
+    except Exception:
+        pass
+    return out
+
+
+def batch_cpu_baseline(be, bs) -> dict:
+    """The oracle over independent solves of the batch workload on every host core (one serial
+    Algorithm 1 per thread at a time), on a bounded sample of the 256 sources."""
+    import oracle
+    oracle.build()
+    W = oracle.build_matrix(be.n, be.src, be.dst, be.w, be.directed)
+    cores = os.cpu_count() or 1
+    k = min(len(bs), 4 * cores)
+    t0 = time.perf_counter()
+    _, _, used = oracle.dijkstra_many_threads(W, np.asarray(bs[:k], dtype=np.int32), cores)
+    el = time.perf_counter() - t0
+    return {"value": k / el, "unit": "SSSP/s", "cores": used, "kind": "oracle",
+            "sample": f"{k} of the 256 sources, serial Algorithm 1 per thread on {used} threads, {el:.1f} s"}
+
+
+def serve_cpu_baseline(graphgen, spec, tr) -> dict:
+    """The oracle over independent requests of the serving trace on every host core: the first
+    3 x cores requests (their graphs built beforehand, as the GPU's are resident), one serial
+    Algorithm 1 per thread at a time."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    R = min(len(tr.req_graph), 3 * cores)
+    mats = {}
+    for r in range(R):
+        gi = int(tr.req_graph[r])
+        if gi not in mats:
+            e = graphgen.bernoulli(int(tr.graph_n[gi]), float(tr.graph_p[gi]), spec["wlo"], spec["whi"],
+                                   int(tr.graph_seed[gi]))
+            mats[gi] = oracle.build_matrix(e.n, e.src, e.dst, e.w, False)
+            del e
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda r: oracle.dijkstra(mats[int(tr.req_graph[r])], int(tr.req_source[r])), range(R)))
+    el = time.perf_counter() - t0
+    del mats
+    return {"value": R / el, "unit": "solves/s", "cores": min(cores, R), "kind": "oracle",
+            "sample": f"the trace's first {R} requests ({len(set(int(x) for x in tr.req_graph[:R]))} graphs), "
+                      f"serial Algorithm 1 per thread on {min(cores, R)} threads, {el:.1f} s"}
 
 
 if __name__ == "__main__":

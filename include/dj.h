@@ -211,14 +211,17 @@ int dj_last_phases(void);
  * allocation, or processes whose caching allocator already reserved nearly
  * all of HBM.  It runs the same grid-engine kernel and gives the same dist
  * and pred as dj_sssp, but its scratch (barrier and candidate counters,
- * per-CTA partials and the two candidate lists, 2 * 8 * pitch bytes) lives in
- * one fixed 4 MiB array compiled into the library: every GPU that loads the
- * library holds those 4 MiB until the process exits.  Graphs whose scratch
- * does not fit (n above about 261,000) are rejected with DJ_EINVAL.
+ * per-CTA partials and two candidate lists of 16 bytes per column, about
+ * 2 * 16 * pitch bytes) lives in one fixed 4 MiB array compiled into the
+ * library: every GPU that loads the library holds those 4 MiB until the
+ * process exits.  Graphs whose scratch does not fit are rejected with
+ * DJ_EINVAL, whose message names this device's limit: n up to 130,720 on a
+ * 152-SM GB300 (the bound moves by a few hundred with the SM count).
  *   g, source, dist, pred, stream: as dj_sssp (dist/pred DEVICE pointers).
  * The call allocates no device memory: it issues two small cudaMemsetAsync
  * calls (clearing the counters and setting dist[source] = -1) and one kernel
- * launch on `stream`.  Asynchronous: once the stream has passed the kernel,
+ * launch on `stream`.  DJ_EUNSUPPORTED if the slice layout cannot be resident
+ * on every SM at once.  Asynchronous: once the stream has passed the kernel,
  * dist[source] == 0 means the solve completed; dist[source] == -1 means a
  * bounded in-kernel wait ran out and the outputs are not valid.
  * The first call on each device performs a one-time set-up (it looks up the

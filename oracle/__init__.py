@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp], check=True)
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-pthread", _SRC, "-o", tmp], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -53,6 +53,8 @@ def _load():
             lib.orc_dijkstra.argtypes = [i32, p, i64, i32, p, p]
             lib.orc_dijkstra_many.restype = None
             lib.orc_dijkstra_many.argtypes = [i32, p, i64, i32, p, p, p]
+            lib.orc_dijkstra_many_mt.restype = ctypes.c_int32
+            lib.orc_dijkstra_many_mt.argtypes = [i32, p, i64, i32, p, p, p, i32]
             _lib = lib
         return _lib
 
@@ -106,4 +108,21 @@ def dijkstra_many(G: np.ndarray, sources):
     return dist, pred
 
 
-__all__ = ["INF", "build", "build_matrix", "dijkstra", "dijkstra_many"]
+def dijkstra_many_threads(G: np.ndarray, sources, threads: int = 0):
+    """dijkstra_many with the independent solves spread over host threads (0 = every core).
+    Returns (dist, pred, threads_used); each solve is the same serial Algorithm 1."""
+    G = _c(G)
+    n = G.shape[0]
+    s = _c(sources)
+    if s.size and (s.min() < 0 or s.max() >= n):
+        raise ValueError("source out of range")
+    k = s.shape[0]
+    if threads <= 0:
+        threads = os.cpu_count() or 1
+    dist = np.empty((k, n), dtype=np.int32)
+    pred = np.empty((k, n), dtype=np.int32)
+    used = _load().orc_dijkstra_many_mt(n, _ptr(G), G.shape[1], k, _ptr(s), _ptr(dist), _ptr(pred), int(threads))
+    return dist, pred, int(used)
+
+
+__all__ = ["INF", "build", "build_matrix", "dijkstra", "dijkstra_many", "dijkstra_many_threads"]

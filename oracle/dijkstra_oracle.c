@@ -23,6 +23,7 @@
  *     G[u][v] only.
  *   - Sums dist[u] + G[u][v] are formed in 64-bit so that they are exact.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -80,4 +81,50 @@ void orc_dijkstra_many(int32_t n, const int32_t* G, int64_t ld, int32_t k, const
                        int32_t* dist, int32_t* pred) {
   for (int32_t i = 0; i < k; ++i)
     orc_dijkstra(n, G, ld, s[i], dist + (int64_t)i * n, pred + (int64_t)i * n);
+}
+
+/* The same independent solves spread over `threads` host threads: thread t
+ * runs orc_dijkstra for the sources t, t + threads, t + 2 threads, ...  Only
+ * the scheduling differs from orc_dijkstra_many; every solve is the serial
+ * Algorithm 1 above, and its outputs are written to the same places.
+ * Returns the number of threads actually used (1 if threads could not be
+ * started, in which case the solves run on the calling thread). */
+typedef struct {
+  int32_t n, k, t, threads;
+  const int32_t* G;
+  int64_t ld;
+  const int32_t* s;
+  int32_t* dist;
+  int32_t* pred;
+} orc_task;
+
+static void* orc_worker(void* arg) {
+  const orc_task* a = (const orc_task*)arg;
+  for (int32_t i = a->t; i < a->k; i += a->threads)
+    orc_dijkstra(a->n, a->G, a->ld, a->s[i], a->dist + (int64_t)i * a->n, a->pred + (int64_t)i * a->n);
+  return NULL;
+}
+
+int orc_dijkstra_many_mt(int32_t n, const int32_t* G, int64_t ld, int32_t k, const int32_t* s,
+                         int32_t* dist, int32_t* pred, int32_t threads) {
+  if (threads > k) threads = k;
+  if (threads < 2) {
+    orc_dijkstra_many(n, G, ld, k, s, dist, pred);
+    return 1;
+  }
+  pthread_t* tid = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+  orc_task* task = (orc_task*)malloc(sizeof(orc_task) * (size_t)threads);
+  int32_t started = 0;
+  for (int32_t t = 0; t < threads; ++t) {
+    orc_task x = {n, k, t, threads, G, ld, s, dist, pred};
+    task[t] = x;
+    if (pthread_create(&tid[t], NULL, orc_worker, &task[t]) != 0) break;
+    ++started;
+  }
+  for (int32_t t = 0; t < started; ++t) pthread_join(tid[t], NULL);
+  /* sources whose thread never started run here */
+  for (int32_t t = started; t < threads; ++t) orc_worker(&task[t]);
+  free(tid);
+  free(task);
+  return started > 0 ? started : 1;
 }

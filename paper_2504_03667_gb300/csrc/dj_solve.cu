@@ -24,6 +24,7 @@
 #include "dj_common.cuh"
 #include "dj_core.cuh"
 #include "dj_internal.h"
+#include "dj_noalloc_size.h"
 
 namespace dj {
 
@@ -989,9 +990,7 @@ SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* p
 namespace dj {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // 4 MiB
-constexpr size_t kNoAllocCtlBytes = 256;                   // barrier + candidate counters (zeroed per call)
-constexpr size_t kNoAllocWordBytes = 64;                   // error bits + phase count (zeroed per call)
+static_assert(kNoAllocMaxCtas == 32 * kMaxPartialsPerLane, "scratch arithmetic and the decision warp agree");
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -1050,24 +1049,32 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   const int nvec_total = g->pitch / 4;
-  const int G = std::min({dv->num_sms, nvec_total, 32 * kMaxPartialsPerLane});
+  const int G = noalloc_ctas(g->pitch, dv->num_sms);
   const int nwarps = kGridThreads / 32;
   const int nvec_cta = (nvec_total + G - 1) / G;
+  const size_t need = noalloc_scratch_bytes(g->pitch, dv->num_sms);
+  if (need > kNoAllocScratchBytes)
+    return set_error(DJ_EINVAL, "graph too large for dj_sssp_noalloc: it needs " + std::to_string(need) +
+                                    " bytes of scratch and the fixed array holds " +
+                                    std::to_string(kNoAllocScratchBytes) + " (n up to " +
+                                    std::to_string(noalloc_max_pitch(dv->num_sms)) + " on this device)");
   Layout L;
   L.filter = true;
   L.list_cap = std::min(nvec_total * 4, kGridListCap);
   if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, 2, static_cast<size_t>(dv->max_smem_optin) - 1024, &L))
     return rc;
   const size_t part_bytes = static_cast<size_t>(2) * G * sizeof(uint4);
-  const size_t cand_bytes = static_cast<size_t>(2) * G * L.swcap * sizeof(uint4);
-  const size_t need = kNoAllocCtlBytes + kNoAllocWordBytes + part_bytes + cand_bytes;
-  if (need > kNoAllocScratchBytes)
-    return set_error(DJ_EINVAL, "graph too large for dj_sssp_noalloc: it needs " + std::to_string(need) +
-                                    " bytes of scratch and the fixed array holds " +
-                                    std::to_string(kNoAllocScratchBytes) + " (n up to about 261000)");
+  if (static_cast<size_t>(L.swcap) != static_cast<size_t>(noalloc_slice_cap(g->pitch, dv->num_sms)) ||
+      sizeof(uint4) != kNoAllocEntryBytes)
+    return set_error(DJ_EUNSUPPORTED, "internal: scratch layout disagrees with the slice layout");
   void* fn = grid_kernel_for(L.V);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
+  // every CTA must be resident at once (cooperative launch); the query allocates nothing
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, L.smem);
+  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (occ < 1) return set_error(DJ_EUNSUPPORTED, "grid engine cannot be resident");
 
   uint8_t* ws = dv->scratch;
   // the counters and status words must start at zero; dist[source] = -1 until the solve completes

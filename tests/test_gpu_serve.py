@@ -169,3 +169,57 @@ def test_bad_requests(dj, graphs):
         dj.dj_serve_submit(srv, gid, e.n)
     assert ei.value.status == dj.DJ_EINVAL
     srv.destroy()
+
+
+def test_bench_serving_mix_against_oracle(dj, orc):
+    """The benchmark's own serving workload (64 resident graphs, n log-uniform in [512, 16384],
+    p uniform in [0.01, 0.5], 10000 requests) run as the benchmark runs it (every request waiting
+    at t = 0, 512 slots, default clusters): a seeded sample of about 1 in 50 results, covering every
+    power-of-two n bucket and the largest graph, equals the CPU oracle element by element."""
+    import torch
+    spec = graphgen.WORKLOADS["serving_64graphs_10000req"]
+    tr = graphgen.serving_trace(spec["graphs"], spec["requests"], 1.0, spec["seed"])
+    graphs = []
+    for gi in range(spec["graphs"]):
+        e = graphgen.bernoulli(int(tr.graph_n[gi]), float(tr.graph_p[gi]), spec["wlo"], spec["whi"],
+                               int(tr.graph_seed[gi]))
+        graphs.append(dj.dj_load_edges(e.n, e.src, e.dst, e.w, False))
+        del e
+    R = spec["requests"]
+    sample = set(range(0, R, 50))
+    bucket = np.floor(np.log2(tr.graph_n[tr.req_graph])).astype(int)
+    for b in np.unique(bucket):  # every n bucket, even if the stride missed it
+        sample.add(int(np.nonzero(bucket == b)[0][0]))
+    biggest = int(np.argmax(tr.graph_n))
+    for gi in np.nonzero(tr.graph_n > 15000)[0]:  # the largest graphs (clusters of 16, wide copies)
+        sample.update(int(r) for r in np.nonzero(tr.req_graph == gi)[0][:3])
+    outs_d = [None] * R
+    outs_p = [None] * R
+    for r in sample:
+        n = int(tr.graph_n[tr.req_graph[r]])
+        outs_d[r] = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+        outs_p[r] = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+    st = dj.dj_serve(graphs, tr.req_graph, tr.req_source, np.zeros(R), outs_d, outs_p,
+                     dj.make_serve_opts(max_slots=512))
+    assert st["completed"] == R
+    torch.cuda.synchronize()
+    for g in graphs:
+        g.free()
+    assert int(tr.graph_n[biggest]) > 15000
+    by_graph = {}
+    for r in sorted(sample):
+        by_graph.setdefault(int(tr.req_graph[r]), []).append(r)
+    checked = set()
+    for gi, rs in sorted(by_graph.items()):
+        e = graphgen.bernoulli(int(tr.graph_n[gi]), float(tr.graph_p[gi]), spec["wlo"], spec["whi"],
+                               int(tr.graph_seed[gi]))
+        W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+        del e
+        D, Pr, _ = orc.dijkstra_many_threads(W, np.array([tr.req_source[r] for r in rs], dtype=np.int32))
+        for i, r in enumerate(rs):
+            assert np.array_equal(outs_d[r].cpu().numpy(), D[i]), ("dist", r, gi)
+            assert np.array_equal(outs_p[r].cpu().numpy(), Pr[i]), ("pred", r, gi)
+            checked.add(int(bucket[r]))
+        del W
+    assert checked == set(int(b) for b in np.unique(bucket))
+    assert len(sample) >= R // 50

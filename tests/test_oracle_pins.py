@@ -52,6 +52,19 @@ def test_many_matches_single(orc):
         assert np.array_equal(D[i], d) and np.array_equal(Pr[i], p)
 
 
+def test_threaded_many_matches_single(orc):
+    """The threaded driver only schedules independent serial solves: every row equals dijkstra()."""
+    rng = np.random.default_rng(8)
+    G = P.random_matrix(rng, 70, 0.15, tuple(range(1, 9)), False)
+    srcs = np.array([3, 0, 69, 3, 41, 12, 5], dtype=np.int32)
+    for threads in (1, 3, 16):
+        D, Pr, used = orc.dijkstra_many_threads(G, srcs, threads)
+        assert 1 <= used <= min(threads, len(srcs))
+        for i, s in enumerate(srcs):
+            d, p = orc.dijkstra(G, int(s))
+            assert np.array_equal(D[i], d) and np.array_equal(Pr[i], p)
+
+
 def test_fill_rejects_bad_edges(orc):
     one = np.array([0], dtype=np.int32)
     with pytest.raises(ValueError):
