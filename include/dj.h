@@ -149,13 +149,16 @@ typedef struct dj_solve_opts {
   int32_t unroll;         /* rows in flight per warp (1, 2, 4 or 8), 0 = auto */
   int64_t timeout_ns;     /* limit of every in-kernel wait, 0 = 2 s */
   int32_t debug_skip_cta; /* testing only: this CTA leaves before the first grid barrier (-1 = none) */
-  int32_t trace_cap;      /* grid engine profiling: entries of `trace` (0 = no trace) */
-  uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 records 8 words:
-                             %globaltimer at publish start, publish end, barrier arrival, barrier
-                             exit, decision end, relaxation end, commit end, then the phase's
-                             candidate count (low 32 bits) and CTA 0's live column groups (high
-                             32 bits); the last two entries get CTA 0's kernel entry and exit
-                             times (trace_cap >= 10); unused entries are left as is */
+  int32_t trace_cap;      /* profiling: entries of `trace` (0 = no trace) */
+  uint64_t* trace;        /* DEVICE pointer to trace_cap uint64: per phase, CTA 0 (grid engine) or
+                             rank 0 (cluster engine) records 8 words.  Grid engine: %globaltimer at
+                             publish start, publish end, barrier arrival, barrier exit, decision
+                             end, relaxation end, commit end, then the phase's candidate count
+                             (low 32 bits) and CTA 0's live column groups (high 32 bits).  Cluster
+                             engine: publish start, publish end, cluster barrier exit, decision
+                             end, staging end, relaxation end (rank 0's warps), commit end, the
+                             candidate count.  The last two entries get the kernel's (solve's)
+                             entry and exit times (trace_cap >= 10); unused entries are left as is */
   int32_t settle;         /* phase mode's settle bounds: DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN */
   int32_t live;           /* grid engine column filter.  A settled row u offers column v at least
                              max(L, m + minin[v]), so a column whose stored dist is below that can
@@ -182,8 +185,17 @@ void dj_solve_opts_init(dj_solve_opts* opts);
 
 /* One solve of Algorithm 1 from `source` on graph g.
  *   dist, pred  DEVICE pointers to n int32 each (caller-owned), written by the kernel.
- * Asynchronous on `stream`.  Errors: DJ_EINVAL (source out of range, NULL),
- * DJ_ECUDA (launch failed); a device-side timeout shows at dj_sync(). */
+ * Asynchronous on `stream`: one kernel launch.  The grid engine keeps a small
+ * workspace per (device, stream) -- about 32 bytes per matrix column plus 16 *
+ * pitch bytes with the row split, at least 1 MiB -- created on the first solve
+ * on that stream (a cudaMalloc) and grown, after synchronising the stream,
+ * when a larger graph comes; solves on one stream share it in stream order,
+ * and it is held until the process exits.  While `stream` is being captured
+ * into a CUDA graph the solve instead allocates and frees its workspace in
+ * stream order (the graph owns it).  The cluster engine (small graphs) needs
+ * no workspace: its solve descriptor travels in the launch's parameters.
+ * Errors: DJ_EINVAL (source out of range, NULL), DJ_ECUDA (launch failed); a
+ * device-side timeout shows at dj_sync(). */
 int dj_sssp(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
 int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                const dj_solve_opts* opts, uint64_t stream);
@@ -200,7 +212,10 @@ int dj_sssp_host(const dj_graph* g, int32_t source, int32_t* dist_host, int32_t*
 int dj_sync(uint64_t stream);
 
 /* Phases (fused relaxation passes) taken by the last completed solve launched
- * by dj_sssp/dj_sssp_ex on this device; -1 if unknown.  Call after dj_sync. */
+ * by dj_sssp/dj_sssp_ex on this device (either engine); -1 if unknown.  Call
+ * after dj_sync.  The count is one word per device written by every single
+ * solve: with solves running concurrently on several streams it reports
+ * whichever of them finished last. */
 int dj_last_phases(void);
 
 /* Allocation-free single solve.  The paper has no counterpart: this entry
@@ -274,9 +289,12 @@ typedef struct dj_batch_opts {
 
 void dj_batch_opts_init(dj_batch_opts* opts);
 
-/* A prepared batch: the descriptor table lives on the device, so launching it
- * is a single kernel launch plus a 64-byte memset, both capturable in a CUDA
- * graph.  The caller keeps the graphs and result buffers alive while launched. */
+/* A prepared batch: the descriptor table and the queue words live on the
+ * device, so launching it is a single kernel launch (capturable in a CUDA
+ * graph): the last cluster of each launch puts the queue back to zero for the
+ * next one.  Launches of one batch must not overlap (one stream, or
+ * synchronise between them).  The caller keeps the graphs and result buffers
+ * alive while launched. */
 typedef struct dj_batch dj_batch;
 int dj_batch_create(const dj_graph* const* graphs, const int32_t* sources, int32_t k,
                     int32_t* const* dist, int32_t* const* pred, const dj_batch_opts* opts,

@@ -58,6 +58,46 @@ int get_ctx(DevCtx** out) {
   return DJ_OK;
 }
 
+static std::mutex g_ws_mu;
+constexpr size_t kMaxStreamWorkspaces = 64;
+
+int stream_workspace(DevCtx* ctx, cudaStream_t st, size_t bytes, size_t zero_bytes, uint8_t** out) {
+  *out = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+  // a captured graph may be replayed on any stream, alongside other solves: it gets its own
+  // stream-ordered allocation instead of this stream's buffer
+  if (cap != cudaStreamCaptureStatusNone) return DJ_OK;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  StreamWs* w = nullptr;
+  for (auto& x : ctx->ws)
+    if (x.stream == st) w = &x;
+  if (w && w->bytes >= bytes) {
+    *out = w->ptr;
+    return DJ_OK;
+  }
+  if (!w) {
+    if (ctx->ws.size() >= kMaxStreamWorkspaces) return DJ_OK;
+    ctx->ws.push_back(StreamWs{st, nullptr, 0});
+    w = &ctx->ws.back();
+  } else {
+    e = cudaStreamSynchronize(st);  // earlier solves on st may still use the old buffer
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize(workspace growth)");
+    cudaFree(w->ptr);
+    w->ptr = nullptr;
+    w->bytes = 0;
+  }
+  const size_t want = std::max(bytes, size_t(1) << 20);
+  e = cudaMalloc(&w->ptr, want);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(stream workspace)");
+  e = cudaMemsetAsync(w->ptr, 0, std::min(zero_bytes, want), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(stream workspace)");
+  w->bytes = want;
+  *out = w->ptr;
+  return DJ_OK;
+}
+
 }  // namespace dj
 
 using namespace dj;
@@ -117,20 +157,12 @@ static int solve_cluster_single(const dj_graph* g, int32_t source, int32_t* dist
   cl.clusters = 1;
   SolveDesc d = make_desc(g, source, dist, pred, o.mode == DJ_MODE_PLAIN ? 1 : 0);
   if (o.settle == DJ_SETTLE_OUT) d.use_in = 0;
-  uint8_t* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, 128, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(cluster workspace)");
-  e = cudaMemcpyAsync(ws, &d, sizeof(d), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_error(e, "descriptor copy");
-  int rc = launch_cluster(reinterpret_cast<SolveDesc*>(ws), 1, g->n, g->pitch, reinterpret_cast<uint32_t*>(ws + 64),
-                          cl, st);
-  cudaFreeAsync(ws, st);
-  if (rc == DJ_OK) {
-    // keep the "phases" word meaningful only for the grid engine
-    DevCtx* ctx = nullptr;
-    if (get_ctx(&ctx) == DJ_OK) cudaMemsetAsync(ctx->words + 1, 0xFF, sizeof(uint32_t), st);
-  }
-  return rc;
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  // one cluster, the descriptor in the kernel's parameters: a single launch, no device memory
+  ClusterPlan plan;
+  if (int rc = plan_cluster(g->pitch, cl, 1, &plan, kJobsSingle)) return rc;
+  return run_cluster_single(plan, d, ctx->words + 1, o.trace, o.trace ? o.trace_cap : 0, st);
 }
 
 extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts* opts,
@@ -279,6 +311,13 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
     return set_error(DJ_ENOMEM, "cudaMalloc(batch descriptors)");
   }
   b->queue = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(b->descs) + static_cast<size_t>(std::max(k, 1)) * sizeof(SolveDesc));
+  // the queue words start at zero; every launch's last cluster puts them back (no memset per launch)
+  e = cudaMemset(b->queue, 0, 64);
+  if (e != cudaSuccess) {
+    cudaFree(b->descs);
+    delete b;
+    return cuda_error(e, "cudaMemset(batch queue)");
+  }
   if (k > 0) {
     e = cudaMemcpy(b->descs, h.data(), static_cast<size_t>(k) * sizeof(SolveDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -311,7 +350,7 @@ extern "C" int dj_batch_launch(dj_batch* b, uint64_t stream) {
   clear_error();
   if (!b) return set_error(DJ_EINVAL, "NULL batch");
   if (b->k == 0) return DJ_OK;
-  return run_cluster(b->plan, b->descs, b->k, b->queue, reinterpret_cast<cudaStream_t>(stream));
+  return run_cluster(b->plan, b->descs, b->k, b->queue, reinterpret_cast<cudaStream_t>(stream), false);
 }
 
 extern "C" int dj_batch_free(dj_batch* b) {

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/dj.h"
 
@@ -48,6 +49,14 @@ struct SolveDesc {
 };
 static_assert(sizeof(SolveDesc) == 64, "descriptor layout");
 
+// A workspace kept for one stream: solves enqueued on the same stream run one
+// after another, so they can share it without any per-solve allocation.
+struct StreamWs {
+  cudaStream_t stream = nullptr;
+  uint8_t* ptr = nullptr;
+  size_t bytes = 0;
+};
+
 struct DevCtx {
   int device = -1;
   int num_sms = 0;
@@ -55,6 +64,7 @@ struct DevCtx {
   int coop = 0;
   int cluster_launch = 0;
   uint32_t* words = nullptr;  // device: [0] error bits, [1] phases of the last single solve
+  std::vector<StreamWs> ws;   // per-stream workspaces of the grid engine (see stream_workspace)
 };
 
 // error reporting (thread-local message)
@@ -64,6 +74,13 @@ void clear_error();
 
 // per-device context of the current device (created on first use)
 int get_ctx(DevCtx** out);
+
+// A device buffer of at least `bytes` kept for stream `st` (its first
+// `zero_bytes` zeroed on `st` when the buffer is created or grown), so that
+// back-to-back solves on one stream allocate nothing.  Growing synchronises
+// `st` once.  *out is nullptr when the stream is being captured or the table
+// of streams is full: the caller then allocates per call, stream-ordered.
+int stream_workspace(DevCtx* ctx, cudaStream_t st, size_t bytes, size_t zero_bytes, uint8_t** out);
 
 inline uint32_t host_bits_for(uint32_t n) {
   uint32_t b = 1;
@@ -112,8 +129,20 @@ struct ClusterPlan {
   int amerge = 0;  // row groups merge through shared-memory atomicMin into one key per column
   uint32_t* words = nullptr;
 };
-int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve = false);
-int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st);
+// where a cluster launch takes its solves: a device table (batch), the serving
+// ring, or one descriptor passed in the kernel's parameters
+constexpr int kJobsBatch = 0;
+constexpr int kJobsServe = 1;
+constexpr int kJobsSingle = 2;
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, int kind = kJobsBatch);
+// queue: two device words (next solve, exit count), zero when the launch starts; with
+// zero_queue the launch zeroes them first, otherwise the previous launch left them zero
+int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st,
+                bool zero_queue);
+// one solve on one cluster, its descriptor in the kernel parameters (no device memory); rank 0
+// writes the phase count to *phases_out, and the per-phase timeline to trace when given
+int run_cluster_single(const ClusterPlan& plan, const SolveDesc& d, uint32_t* phases_out, uint64_t* trace,
+                       int32_t trace_cap, cudaStream_t st);
 
 // The serving request ring as the persistent kernel sees it (device-usable
 // addresses of mapped pinned host memory, plus the device-side head).

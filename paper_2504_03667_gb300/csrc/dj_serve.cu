@@ -113,7 +113,7 @@ int ensure_plan(dj_server* s) {
   ClusterLaunch cl;
   cl.cluster_size = s->opts.cluster_size > 0 ? s->opts.cluster_size : heuristic_cluster(pitch);
   cl.clusters = s->opts.clusters;
-  if (int rc = plan_cluster(pitch, cl, 0, &s->plan, true)) return rc;
+  if (int rc = plan_cluster(pitch, cl, 0, &s->plan, kJobsServe)) return rc;
   s->plan_pitch = pitch;
   s->plan_valid = true;
   return DJ_OK;

@@ -71,13 +71,36 @@ constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CT
 constexpr int kRowSplitCpt = 8;          // row split: 4-column groups per thread per column chunk
 constexpr int kColPassMin = 1024;        // gather column pass: phases with at least this many candidates
 
-template <int V, int U, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ BlockScratch sc;
-  __shared__ Decision s_dec;
-  __shared__ uint32_t s_flag;
+// Control words of a grid launch (the first 16 words of its workspace): the
+// barrier's arrival counter, the abort flag, the row split's snapshot counter
+// and the exit counter.  They are zero when a launch starts: zeroed once when
+// the workspace is created, and put back to zero by the last CTA to leave
+// each launch (grid_exit), so back-to-back solves on one stream need no
+// memset between them.
+constexpr int kCtlBarrier = 0;
+constexpr int kCtlAbort = 5;
+constexpr int kCtlSnapshots = 8;
+constexpr int kCtlExit = 12;
+constexpr int kCtlWords = 16;
 
+// Every CTA calls this once, after its last access of the control words (all
+// threads, uniform control flow).  The CTA that arrives last zeroes them for
+// the next launch on the stream, which starts only after this one has ended.
+__device__ __forceinline__ void grid_exit(uint32_t* ctl) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's barrier arrivals precede its exit count
+    if (atomicAdd(ctl + kCtlExit, 1u) == gridDim.x - 1) {
+      __threadfence();
+#pragma unroll
+      for (int i = 0; i < kCtlWords; ++i) ctl[i] = 0u;
+    }
+  }
+}
+
+template <int V, int U>
+__device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, BlockScratch& sc, Decision& s_dec,
+                                           uint32_t& s_flag, uint32_t& s_rem) {
   const int G = gridDim.x, b = blockIdx.x;
   if (p.trace && b == 0 && threadIdx.x == 0 && p.trace_cap >= 10) p.trace[p.trace_cap - 2] = global_ns();  // entry
   Slice s;
@@ -149,8 +172,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   fence_mbar_init();
   __syncthreads();
 
-  uint32_t* bar = p.ctl;
-  uint32_t* abort_flag = p.ctl + 5;
+  uint32_t* bar = p.ctl + kCtlBarrier;
+  uint32_t* abort_flag = p.ctl + kCtlAbort;
   if (p.rs_min > 0) {  // row-split merge keys of this slice, ordered before use by the first barrier
     for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
       p.gkey[s.c0 + j] = ~0ull;
@@ -160,7 +183,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   Part part;
   slice_partial(s, part);
   uint32_t phase = 0, nbar = 0, rs_gt = 0, rs_phases = 0;
-  __shared__ uint32_t s_rem;  // unvisited columns that are no candidates, summed over the CTAs
   for (;;) {
     // per-phase timeline of CTA 0 (profiling only): 8 stamps per phase
     uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? p.trace + 8 * phase
@@ -268,10 +290,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
       // this slice's snapshot for the other CTAs' merges, announced without waiting
       for (int j = threadIdx.x; j < s.sw; j += blockDim.x) p.gsnap[s.c0 + j] = snapshot_word(s, j, D);
       __syncthreads();
-      if (threadIdx.x == 0) red_add_release_gpu(p.ctl + 8, 1u);
+      if (threadIdx.x == 0) red_add_release_gpu(p.ctl + kCtlSnapshots, 1u);
       ++rs_phases;
       if (!relax_rows<kRowSplitCpt>(get, total, b, G, p.W, p.pitch, D, p.bits_u, p.gsnap, gk, list, p.list_cap,
-                                    rings, rbar, rs_gt, p.timeout_ns, p.ctl + 8, rs_phases * static_cast<uint32_t>(G),
+                                    rings, rbar, rs_gt, p.timeout_ns, p.ctl + kCtlSnapshots,
+                                    rs_phases * static_cast<uint32_t>(G),
                                     abort_flag, &sc)) {
         atomicOr(p.words, kErrTimeout);
         atomicExch(abort_flag, 1u);
@@ -341,20 +364,58 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   }
 }
 
+template <int V, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ BlockScratch sc;
+  __shared__ Decision s_dec;
+  __shared__ uint32_t s_flag;
+  __shared__ uint32_t s_rem;  // unvisited columns that are no candidates, summed over the CTAs
+  grid_solve<V, U>(p, smem, sc, s_dec, s_flag, s_rem);  // returns early (uniformly per CTA) on a timeout
+  grid_exit(p.ctl);
+}
+
 // ============================================================ cluster engine
 
 // Where the cluster engine gets its solves.  fetch() and complete() run on
 // thread 0 of cluster rank 0 only.
 struct BatchJobs {
   const SolveDesc* descs;
-  uint32_t* queue;  // [0] next solve index (zeroed before launch)
+  uint32_t* queue;  // [0] next solve index, [1] exit count: both zero when a launch starts
   int32_t k;
-  __device__ bool fetch(uint32_t* job) const {
+  __device__ bool fetch(uint32_t* job, uint32_t) const {
     *job = atomicAdd(queue, 1u);
     return *job < static_cast<uint32_t>(k);
   }
   __device__ SolveDesc desc(uint32_t job) const { return descs[job]; }
-  __device__ void complete(uint32_t) const {}
+  __device__ void complete(uint32_t, uint32_t) const {}
+  // once per cluster, by rank 0, after its last fetch: the last cluster to leave zeroes the
+  // queue for the next launch (the stream starts it only after this one has ended)
+  __device__ void leave() const {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1u) == nclusters_x() - 1) {
+      __threadfence();
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
+  }
+};
+
+// One solve whose descriptor travels in the kernel's parameters: no table,
+// queue or memset on the device.  Launched as a single cluster; its rank 0
+// records the phase count in the per-device word.
+struct SingleJob {
+  SolveDesc d;
+  uint32_t* phases_out;
+  __device__ bool fetch(uint32_t* job, uint32_t iter) const {
+    *job = 0;
+    return iter == 0 && cluster_id_x() == 0;
+  }
+  __device__ SolveDesc desc(uint32_t) const { return d; }
+  __device__ void complete(uint32_t, uint32_t phases) const {
+    if (phases_out) *phases_out = phases;
+  }
+  __device__ void leave() const {}
 };
 
 // Serving: requests arrive in a ring of descriptors in mapped pinned host
@@ -372,7 +433,7 @@ struct ServeJobs {
   uint32_t* head;         // device memory
   uint32_t cap_mask;
   int64_t idle_ns;
-  __device__ bool fetch(uint32_t* job) const {
+  __device__ bool fetch(uint32_t* job, uint32_t) const {
     uint64_t t0 = global_ns();
     for (;;) {
       if (ld_acquire_sys(stop)) return false;
@@ -398,14 +459,17 @@ struct ServeJobs {
     for (int i = 0; i < 4; ++i) d4[i] = __ldcv(s4 + i);
     return d;
   }
-  __device__ void complete(uint32_t job) const {
+  __device__ void complete(uint32_t job, uint32_t) const {
     __threadfence_system();
     st_release_sys(done + (job & cap_mask), job + 1);
   }
+  __device__ void leave() const {}
 };
 
 struct ClusterParams {
   uint32_t* words;  // per-device words: [0] error bits
+  uint64_t* trace;  // optional per-phase timeline of the first solve (rank 0), as the grid engine's
+  int32_t trace_cap;
   int64_t timeout_ns;
   int32_t swcap;
   int32_t rgs_cap;
@@ -471,11 +535,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
   fence_mbar_init();
   __syncthreads();
 
-  for (;;) {
+  for (uint32_t iter = 0;; ++iter) {
     // next solve: rank 0 takes it from the job source, every CTA reads it through DSMEM
     if (rank == 0 && threadIdx.x == 0) {
       uint32_t j = 0;
-      s_job = jobs.fetch(&j) ? j : 0xFFFFFFFFu;
+      s_job = jobs.fetch(&j, iter) ? j : 0xFFFFFFFFu;
+      if (s_job == 0xFFFFFFFFu) jobs.leave();
     }
     cluster_sync_all();
     if (threadIdx.x == 0) s_jobl = (rank == 0) ? s_job : ld_dsmem_u32(dsmem_addr(&s_job, 0));
@@ -485,6 +550,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       cluster_sync_all();  // rank 0's s_job stays readable until everyone has it
       return;
     }
+    // per-phase timeline of the first solve (rank 0, thread 0; profiling only)
+    uint64_t* const trace = (p.trace && iter == 0 && rank == 0 && threadIdx.x == 0) ? p.trace : nullptr;
+    if (trace && p.trace_cap >= 10) trace[p.trace_cap - 2] = global_ns();
     const SolveDesc d = jobs.desc(job);
     const int nvec_total = static_cast<int>(d.pitch / 4);
     const int v0 = static_cast<int>(static_cast<int64_t>(rank) * nvec_total / C);
@@ -506,6 +574,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     slice_partial(s, part);
     uint32_t phase = 0;
     for (;;) {
+      uint64_t* tr = (trace && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? trace + 8 * phase : nullptr;
+      if (tr) tr[0] = global_ns();
       uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
       uint64_t key;
       uint32_t Lc;
@@ -513,7 +583,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       if (threadIdx.x == 0)
         s_part[phase & 1] =
             make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
+      if (tr) tr[1] = global_ns();
       cluster_sync_all();
+      if (tr) tr[2] = global_ns();
       if (warp == 0) {
         uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
         if (static_cast<uint32_t>(lane) < C) x = ld_dsmem_u32x4(dsmem_addr(&s_part[phase & 1], lane));
@@ -540,10 +612,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       }
       __syncthreads();
       const Decision D = s_dec;
+      const int total = static_cast<int>(s_off[C]);
+      if (tr) {
+        tr[3] = global_ns();
+        tr[7] = static_cast<uint64_t>(total);
+      }
       if (D.m >= kInf) break;
       Best<V> best;
       best_init<V>(best, s, t, D, d.bits_u);
-      const int total = static_cast<int>(s_off[C]);
       const int Cn = static_cast<int>(C);
       bool ok;
       if (d.plain) {  // Algorithm 1's single row a: no candidate list to read
@@ -564,14 +640,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
                 return make_uint4(e.x, e.y, in_key(e.y, static_cast<uint32_t>(__ldg(minin_g + e.x))), 0u);
               },
               seg, min(total, seg + p.list_cap), D, bu, list, &sc);
+          if (tr && seg == 0) tr[4] = global_ns();
           ok = relax_pull<V, U>([list, D, bu](int i) { return staged_entry(list, i, D, bu); }, cnt, s, t, d.W,
                                 d.pitch, D, bu, ring, slot_rows, slot_tb, p.timeout_ns, best) &&
                ok;
           __syncthreads();  // the list is rewritten by the next segment
         }
       }
+      if (tr) tr[5] = global_ns();
       if (!ok) atomicOr(p.words, kErrTimeout);
       commit_partial<V>(s, t, D, merge, d.bits_u, best, part, p.amerge != 0);
+      if (tr) tr[6] = global_ns();
       ++phase;
     }
     slice_write_out(s, d.n, d.dist, d.pred);
@@ -579,7 +658,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     __syncthreads();
     if (threadIdx.x == 0) __threadfence_system();
     cluster_sync_all();
-    if (rank == 0 && threadIdx.x == 0) jobs.complete(job);
+    if (rank == 0 && threadIdx.x == 0) {
+      jobs.complete(job, phase);
+      if (trace && p.trace_cap >= 10) trace[p.trace_cap - 1] = global_ns();
+    }
   }
 }
 
@@ -690,13 +772,19 @@ void* grid_kernel_for(int v) {
   }
   return nullptr;
 }
-void* cluster_kernel_for(int v, bool serve = false) {
+template <class Jobs>
+void* cluster_kernel_v(int v) {
   switch (v) {
-    case 1: return serve ? cluster_kernel<1, ServeJobs>() : cluster_kernel<1, BatchJobs>();
-    case 2: return serve ? cluster_kernel<2, ServeJobs>() : cluster_kernel<2, BatchJobs>();
-    case 4: return serve ? cluster_kernel<4, ServeJobs>() : cluster_kernel<4, BatchJobs>();
+    case 1: return cluster_kernel<1, Jobs>();
+    case 2: return cluster_kernel<2, Jobs>();
+    case 4: return cluster_kernel<4, Jobs>();
   }
   return nullptr;
+}
+void* cluster_kernel_for(int v, int kind = kJobsBatch) {
+  if (kind == kJobsServe) return cluster_kernel_v<ServeJobs>(v);
+  if (kind == kJobsSingle) return cluster_kernel_v<SingleJob>(v);
+  return cluster_kernel_v<BatchJobs>(v);
 }
 
 
@@ -746,10 +834,17 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                                                                                               : auto_rowsplit_min(g->n);
   const size_t snap_bytes = rs_min > 0 ? static_cast<size_t>(g->pitch) * 4 : 0;  // pitch is a multiple of 4
   const size_t gkey_bytes = rs_min > 0 ? static_cast<size_t>(2) * g->pitch * 8 : 0;
+  // the stream's kept workspace (its control words are zero between launches: see grid_exit),
+  // or one allocated for this call
+  const size_t ws_bytes = ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes;
   uint8_t* ws = nullptr;
-  e = cudaMallocAsync(&ws, ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(grid workspace)");
-  cudaMemsetAsync(ws, 0, ctl_bytes, st);
+  if (int rc = stream_workspace(ctx, st, ws_bytes, ctl_bytes, &ws)) return rc;
+  const bool own_ws = ws == nullptr;
+  if (own_ws) {
+    e = cudaMallocAsync(&ws, ws_bytes, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(grid workspace)");
+    cudaMemsetAsync(ws, 0, ctl_bytes, st);
+  }
 
   GridParams p;
   p.W = g->W;
@@ -792,7 +887,7 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.sym = g->directed ? 0 : 1;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
-  cudaFreeAsync(ws, st);
+  if (own_ws) cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
   return DJ_OK;
 }
@@ -869,11 +964,12 @@ bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl) {
   return ok;
 }
 
-int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, bool serve) {
+int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterPlan* plan, int kind) {
   if (cl.cluster_size < 1 || cl.cluster_size > 16) return set_error(DJ_EINVAL, "cluster size must be 1..16");
+  const bool serve = kind == kJobsServe;
   Layout L;
   if (int rc = cluster_layout(max_pitch, cl, &L)) return rc;
-  void* fn = cluster_kernel_for(L.V, serve);
+  void* fn = cluster_kernel_for(L.V, kind);
   if (int rc = prepare_cluster(fn, cl, L.smem)) return rc;
   int Q = cl.clusters;
   if (Q <= 0) {
@@ -918,6 +1014,8 @@ static int launch_plan(const ClusterPlan& plan, void** args, cudaStream_t st) {
 static ClusterParams params_of(const ClusterPlan& plan) {
   ClusterParams p;
   p.words = plan.words;
+  p.trace = nullptr;
+  p.trace_cap = 0;
   p.timeout_ns = 2000000000LL;
   p.swcap = plan.swcap;
   p.rgs_cap = plan.rgs_cap;
@@ -929,9 +1027,12 @@ static ClusterParams params_of(const ClusterPlan& plan) {
   return p;
 }
 
-int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(queue)");
+int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st,
+                bool zero_queue) {
+  if (zero_queue) {  // a fresh queue; a prepared batch's is zeroed once and reset by each launch's last cluster
+    cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(queue)");
+  }
   ClusterParams p = params_of(plan);
   BatchJobs jobs;
   jobs.descs = descs_dev;
@@ -959,7 +1060,19 @@ int launch_cluster(const SolveDesc* descs_dev, int32_t k, int32_t /*max_n*/, int
                    const ClusterLaunch& cl, cudaStream_t st) {
   ClusterPlan plan;
   if (int rc = plan_cluster(max_pitch, cl, k, &plan)) return rc;
-  return run_cluster(plan, descs_dev, k, queue, st);
+  return run_cluster(plan, descs_dev, k, queue, st, true);
+}
+
+int run_cluster_single(const ClusterPlan& plan, const SolveDesc& d, uint32_t* phases_out, uint64_t* trace,
+                       int32_t trace_cap, cudaStream_t st) {
+  ClusterParams p = params_of(plan);
+  p.trace = trace;
+  p.trace_cap = trace ? trace_cap : 0;
+  SingleJob job;
+  job.d = d;
+  job.phases_out = phases_out;
+  void* args[] = {&p, &job};
+  return launch_plan(plan, args, st);
 }
 
 SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, int plain) {
