@@ -631,7 +631,15 @@ def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
     c1.record(stream)
     dj.dj_sync(stream)
     s_per = c0.elapsed_time(c1) / 1e3 / reps
-    # phases of one solve from the workload's own source (grid engine only reports them)
+    # latency of one solve on its own: events around a single call, the stream idle before it
+    lat = []
+    for i in range(20):
+        c0.record(stream)
+        dj.dj_sssp(g, srcs[i % 16], d, p, stream)
+        c1.record(stream)
+        c1.synchronize()
+        lat.append(c0.elapsed_time(c1) * 1e3)
+    # phases of one solve from the workload's own source
     dj.dj_sssp(g, srcs[0], d, p, stream)
     dj.dj_sync(stream)
     phases = dj.dj_last_phases()
@@ -640,6 +648,7 @@ def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
     peak, peak_kind = _peaks()
     achieved = n * n * 4 / s_per / 1e9
     return {"value": 1.0 / s_per, "unit": "SSSP/s", "us_per_solve": 1e6 * s_per, "solves_timed": reps,
+            "latency_us_alone": statistics.median(lat),
             "phases_first_source": phases if phases >= 0 else None,
             "engine": "grid" if (n >= 4096 or (n >= 2560 and info["entries"] * 4 >= n * n)) else "cluster",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

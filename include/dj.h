@@ -114,11 +114,15 @@ int dj_load_dense(int32_t n, const int32_t* W, int64_t ld, int w_on_device, uint
                   dj_graph** out);
 
 /* Overwrite an existing graph's matrix with a new n x n matrix of the same n
- * (host pointer W, row stride ld), then recompute its row minima.  This is the
- * host-to-device matrix copy of the paper's CUDA accounting (Section III-C,
- * "Memory allocation and data transfer") without a new allocation.  The copy
- * is asynchronous on `stream` when W is pinned; entries are not re-validated
- * (callers pass matrices that came from dj_graph_download or a validated load). */
+ * (host pointer W, row stride ld), then recompute its row and column minima and
+ * tie sources.  This is the host-to-device matrix copy of the paper's CUDA
+ * accounting (Section III-C, "Memory allocation and data transfer") without a
+ * new allocation.  The copy is asynchronous on `stream` when W is pinned;
+ * entries are not re-validated (callers pass matrices that came from
+ * dj_graph_download or a validated load, symmetric if the graph was loaded
+ * undirected, whose column minima are taken from the row minima).  The next
+ * solve of g waits for the kernels before it on its stream before it reads the
+ * matrix. */
 int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64_t stream);
 
 /* Copy the n x n matrix to HOST memory W (row stride ld >= n); synchronous. */

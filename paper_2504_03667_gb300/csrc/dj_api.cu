@@ -162,7 +162,10 @@ static int solve_cluster_single(const dj_graph* g, int32_t source, int32_t* dist
   // one cluster, the descriptor in the kernel's parameters: a single launch, no device memory
   ClusterPlan plan;
   if (int rc = plan_cluster(g->pitch, cl, 1, &plan, kJobsSingle)) return rc;
-  return run_cluster_single(plan, d, ctx->words + 1, o.trace, o.trace ? o.trace_cap : 0, st);
+  // right after an upload the solve waits for the kernels before it before reading the graph
+  const bool early = g->upload_pending == 0;
+  const_cast<dj_graph*>(g)->upload_pending = 0;
+  return run_cluster_single(plan, d, ctx->words + 1, o.trace, o.trace ? o.trace_cap : 0, early, st);
 }
 
 extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts* opts,

@@ -54,6 +54,15 @@ __device__ __forceinline__ int4 ld_stream16(const int32_t* p) {
   return v;
 }
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// Let the next kernel on the stream start launching (it waits for this grid
+// where it needs to, with pdl_wait).  Without a dependent launched that way
+// it has no effect.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Wait until the grids this one depends on have completed and their memory
+// is visible; returns at once when the kernel was launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- mbarrier + TMA bulk copies
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

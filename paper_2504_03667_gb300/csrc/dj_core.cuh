@@ -276,17 +276,35 @@ __device__ __forceinline__ void slice_partial(const Slice& s, Part& pt) {
 // the candidates {unvisited v : dist[v] < L_c} u {IN candidates} u {argmin} as
 // (v, dist[v][, IN key]) to `out` (order irrelevant: the relaxation keys are order-free).  sc->cnt[32]
 // must be zero on entry.  Returns the count; all threads get key, Lc, count.
-__device__ __forceinline__ void put_entry(uint4* out, uint32_t v, uint32_t d, uint32_t ik) {
+__device__ __forceinline__ void put_entry(uint4* out, uint32_t v, uint32_t d, uint32_t ik, uint32_t, uint32_t) {
   *out = make_uint4(v, d, ik, 0u);
 }
-__device__ __forceinline__ void put_entry(uint2* out, uint32_t v, uint32_t d, uint32_t) {
-  *out = make_uint2(v, d);  // readers recompute the IN key from minin
+// 8-byte entry (cluster engine): v in the low bits_u bits, and above them v's
+// smallest in-weight saturated to the field (all ones: look it up), so that a
+// reader recomputes the IN key without a dependent global load.  Every finite
+// weight fits: (n - 1) * max weight < 2^31 and n > 2^(bits_u - 1) give
+// max weight < 2^(32 - bits_u).
+__device__ __forceinline__ uint32_t minin_field_max(uint32_t bits_u) { return (1u << (32 - bits_u)) - 1u; }
+__device__ __forceinline__ void put_entry(uint2* out, uint32_t v, uint32_t d, uint32_t, uint32_t minin,
+                                          uint32_t bits_u) {
+  *out = make_uint2(v | (min(minin, minin_field_max(bits_u)) << bits_u), d);
+}
+// The candidate (u, dist[u], IN key) of a packed 8-byte entry (IN key 0, unused,
+// when the IN bound is off).
+__device__ __forceinline__ uint4 unpack_entry(uint2 e, uint32_t bits_u, const int32_t* __restrict__ minin_g,
+                                              bool use_in) {
+  const uint32_t u = e.x & ((1u << bits_u) - 1u);
+  if (!use_in) return make_uint4(u, e.y, 0u, 0u);
+  uint32_t mi = e.x >> bits_u;
+  if (mi == minin_field_max(bits_u)) mi = static_cast<uint32_t>(__ldg(minin_g + u));  // saturated: rare
+  return make_uint4(u, e.y, in_key(e.y, mi), 0u);
 }
 
 template <class Entry>
 __device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bool plain, bool use_in,
                                                const Part& pt, Entry* out, BlockScratch* sc, uint64_t* key_out,
-                                               uint32_t* Lc_out, uint32_t* unvis_out = nullptr) {
+                                               uint32_t* Lc_out, uint32_t* unvis_out = nullptr,
+                                               uint32_t bits_u = 0) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   uint64_t k = warp_min_u64(pt.key);
   uint32_t l = warp_min_u32(pt.lc);
@@ -329,7 +347,9 @@ __device__ __forceinline__ int publish_partial(const Slice& s, uint32_t span, bo
         uint32_t pos = 0;
         if (lane == 0) pos = atomicAdd(&sc->cnt[32], static_cast<uint32_t>(__popc(bal)));
         pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (p) put_entry(out + pos + __popc(bal & ((1u << lane) - 1u)), static_cast<uint32_t>(s.c0 + j), d, ik);
+        if (p)
+          put_entry(out + pos + __popc(bal & ((1u << lane) - 1u)), static_cast<uint32_t>(s.c0 + j), d, ik,
+                    s.minin[j], bits_u);
       }
     }
   }

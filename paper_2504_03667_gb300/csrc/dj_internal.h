@@ -29,6 +29,9 @@ struct dj_graph {
   int64_t* row_ptr = nullptr;  // n + 1 edge offsets
   int32_t* col = nullptr;      // nnz targets, sorted within a row
   int32_t* wt = nullptr;       // nnz weights
+  // set by dj_graph_upload: the next solve waits for the kernels before it on its stream
+  // before it reads the matrix (solves otherwise read the graph while the previous kernel ends)
+  int32_t upload_pending = 0;
 };
 
 namespace dj {
@@ -140,9 +143,12 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
 int run_cluster(const ClusterPlan& plan, const SolveDesc* descs_dev, int32_t k, uint32_t* queue, cudaStream_t st,
                 bool zero_queue);
 // one solve on one cluster, its descriptor in the kernel parameters (no device memory); rank 0
-// writes the phase count to *phases_out, and the per-phase timeline to trace when given
+// writes the phase count to *phases_out, and the per-phase timeline to trace when given.
+// Launched as a programmatic dependent of the previous kernel on the stream: it solves while
+// that kernel ends and waits for it only before writing its outputs (and, unless `early`, before
+// reading the graph).
 int run_cluster_single(const ClusterPlan& plan, const SolveDesc& d, uint32_t* phases_out, uint64_t* trace,
-                       int32_t trace_cap, cudaStream_t st);
+                       int32_t trace_cap, bool early, cudaStream_t st);
 
 // The serving request ring as the persistent kernel sees it (device-usable
 // addresses of mapped pinned host memory, plus the device-side head).

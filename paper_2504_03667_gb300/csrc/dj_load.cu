@@ -366,6 +366,7 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
                           static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
                           static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_error(e, "host-to-device matrix copy (upload)");
+  g->upload_pending = 1;
   launch_minima(g, nullptr, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "row minima");

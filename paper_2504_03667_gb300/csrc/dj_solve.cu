@@ -18,6 +18,7 @@
 // The phase logic (what is settled per pass and why it equals Algorithm 1) is
 // in dj_core.cuh.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -371,6 +372,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   __shared__ Decision s_dec;
   __shared__ uint32_t s_flag;
   __shared__ uint32_t s_rem;  // unvisited columns that are no candidates, summed over the CTAs
+  // launched as a programmatic dependent of the previous kernel on the stream: its launch overlaps
+  // that kernel's end, but nothing (graph, workspace, outputs) is touched before it has completed
+  pdl_launch_dependents();
+  pdl_wait();
   grid_solve<V, U>(p, smem, sc, s_dec, s_flag, s_rem);  // returns early (uniformly per CTA) on a timeout
   grid_exit(p.ctl);
 }
@@ -389,6 +394,9 @@ struct BatchJobs {
   }
   __device__ SolveDesc desc(uint32_t job) const { return descs[job]; }
   __device__ void complete(uint32_t, uint32_t) const {}
+  static constexpr bool kTrace = false;
+  __device__ bool early() const { return true; }  // launched the ordinary way: nothing to wait for
+  __device__ void before_write() const {}
   // once per cluster, by rank 0, after its last fetch: the last cluster to leave zeroes the
   // queue for the next launch (the stream starts it only after this one has ended)
   __device__ void leave() const {
@@ -403,10 +411,18 @@ struct BatchJobs {
 
 // One solve whose descriptor travels in the kernel's parameters: no table,
 // queue or memset on the device.  Launched as a single cluster; its rank 0
-// records the phase count in the per-device word.
+// records the phase count in the per-device word.  It is launched as a
+// programmatic dependent of the kernel before it on the stream: it starts
+// while that kernel is still running (every CTA lets its own dependents start
+// at once), solves from the graph, which no kernel writes meanwhile (unless
+// `early_ok` is 0, after an upload: then it waits first), and waits for its
+// predecessor to complete only before it writes dist, pred and the phase
+// count.  So results reach memory in stream order, and back-to-back solves of
+// small graphs overlap on the GPU's idle SMs.
 struct SingleJob {
   SolveDesc d;
   uint32_t* phases_out;
+  int32_t early_ok;
   __device__ bool fetch(uint32_t* job, uint32_t iter) const {
     *job = 0;
     return iter == 0 && cluster_id_x() == 0;
@@ -415,6 +431,9 @@ struct SingleJob {
   __device__ void complete(uint32_t, uint32_t phases) const {
     if (phases_out) *phases_out = phases;
   }
+  static constexpr bool kTrace = true;  // the per-phase timeline is compiled into this kernel only
+  __device__ bool early() const { return early_ok != 0; }
+  __device__ void before_write() const { pdl_wait(); }
   __device__ void leave() const {}
 };
 
@@ -463,6 +482,9 @@ struct ServeJobs {
     __threadfence_system();
     st_release_sys(done + (job & cap_mask), job + 1);
   }
+  static constexpr bool kTrace = false;
+  __device__ bool early() const { return true; }
+  __device__ void before_write() const {}
   __device__ void leave() const {}
 };
 
@@ -534,6 +556,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     for (int j = threadIdx.x; j < p.swcap; j += blockDim.x) merge[j] = kNoKey;
   fence_mbar_init();
   __syncthreads();
+  pdl_launch_dependents();  // the next kernel on the stream may start (it waits where it must)
 
   for (uint32_t iter = 0;; ++iter) {
     // next solve: rank 0 takes it from the job source, every CTA reads it through DSMEM
@@ -551,9 +574,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       return;
     }
     // per-phase timeline of the first solve (rank 0, thread 0; profiling only)
-    uint64_t* const trace = (p.trace && iter == 0 && rank == 0 && threadIdx.x == 0) ? p.trace : nullptr;
+    uint64_t* const trace = (Jobs::kTrace && p.trace && iter == 0 && rank == 0 && threadIdx.x == 0) ? p.trace : nullptr;
     if (trace && p.trace_cap >= 10) trace[p.trace_cap - 2] = global_ns();
     const SolveDesc d = jobs.desc(job);
+    if (!jobs.early()) pdl_wait();  // the kernel before may still be writing the graph
     const int nvec_total = static_cast<int>(d.pitch / 4);
     const int v0 = static_cast<int>(static_cast<int64_t>(rank) * nvec_total / C);
     const int v1 = static_cast<int>(static_cast<int64_t>(rank + 1) * nvec_total / C);
@@ -574,12 +598,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     slice_partial(s, part);
     uint32_t phase = 0;
     for (;;) {
-      uint64_t* tr = (trace && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? trace + 8 * phase : nullptr;
+      uint64_t* tr = (Jobs::kTrace && trace && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? trace + 8 * phase
+                                                                                                 : nullptr;
       if (tr) tr[0] = global_ns();
       uint2* mine = own + static_cast<size_t>(phase & 1) * p.swcap;
       uint64_t key;
       uint32_t Lc;
-      const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, part, mine, &sc, &key, &Lc);
+      const int c = publish_partial(s, d.span, d.plain != 0, d.use_in != 0, part, mine, &sc, &key, &Lc, nullptr,
+                                    d.bits_u);
       if (threadIdx.x == 0)
         s_part[phase & 1] =
             make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, static_cast<uint32_t>(c));
@@ -634,10 +660,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
         for (int seg = 0; seg < total; seg += p.list_cap) {
           const int32_t* minin_g = d.minout + d.n;
           const int cnt = stage_settled(
-              [Cn, minin_g](int i) {
+              [Cn, minin_g, bu, D](int i) {
                 const int r = region_of16(s_off, Cn, i);
                 const uint2 e = ld_dsmem_u32x2(s_addr[r] + 8u * static_cast<uint32_t>(i - static_cast<int>(s_off[r])));
-                return make_uint4(e.x, e.y, in_key(e.y, static_cast<uint32_t>(__ldg(minin_g + e.x))), 0u);
+                return unpack_entry(e, bu, minin_g, D.use_in != 0);
               },
               seg, min(total, seg + p.list_cap), D, bu, list, &sc);
           if (tr && seg == 0) tr[4] = global_ns();
@@ -653,6 +679,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
       if (tr) tr[6] = global_ns();
       ++phase;
     }
+    jobs.before_write();  // results reach memory in stream order
     slice_write_out(s, d.n, d.dist, d.pred);
     // every CTA's outputs are visible system-wide before rank 0 reports completion
     __syncthreads();
@@ -790,6 +817,34 @@ void* cluster_kernel_for(int v, int kind = kJobsBatch) {
 
 }  // namespace
 
+// A cooperative launch (every CTA resident at once), as a programmatic dependent of the
+// previous kernel on the stream when `pdl` (the kernel waits for it before touching memory;
+// only the launch itself overlaps).  If the runtime rejects that pairing, the plain cooperative
+// launch is used from then on.
+static std::atomic<int> g_coop_pdl_ok{1};
+cudaError_t launch_cooperative(void* fn, int G, int threads, void** args, size_t smem, cudaStream_t st, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(G));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (pdl && g_coop_pdl_ok.load()) ? 2 : 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+  if (e != cudaSuccess && cfg.numAttrs == 2) {
+    cudaGetLastError();
+    g_coop_pdl_ok.store(0);
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+  }
+  return e;
+}
+
 int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, const dj_solve_opts& o,
                 cudaStream_t st) {
   DevCtx* ctx = nullptr;
@@ -886,9 +941,9 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
   void* args[] = {&p};
-  e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
+  e = launch_cooperative(fn, G, kGridThreads, args, L.smem, st, true);
   if (own_ws) cudaFreeAsync(ws, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");
+  if (e != cudaSuccess) return cuda_error(e, "cooperative launch (grid engine)");
   return DJ_OK;
 }
 
@@ -993,20 +1048,27 @@ int plan_cluster(int32_t max_pitch, const ClusterLaunch& cl, int32_t k, ClusterP
   return DJ_OK;
 }
 
-static int launch_plan(const ClusterPlan& plan, void** args, cudaStream_t st) {
+static int launch_plan(const ClusterPlan& plan, void** args, cudaStream_t st, bool pdl = false) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(plan.clusters * plan.cluster_size));
   cfg.blockDim = dim3(static_cast<unsigned>(plan.threads));
   cfg.dynamicSmemBytes = plan.smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = plan.cluster_size;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   cudaError_t e = cudaLaunchKernelExC(&cfg, plan.fn, args);
+  if (e != cudaSuccess && pdl) {  // not accepted here: the ordinary launch gives the same results
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, plan.fn, args);
+  }
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchKernelEx(cluster engine)");
   return DJ_OK;
 }
@@ -1064,15 +1126,16 @@ int launch_cluster(const SolveDesc* descs_dev, int32_t k, int32_t /*max_n*/, int
 }
 
 int run_cluster_single(const ClusterPlan& plan, const SolveDesc& d, uint32_t* phases_out, uint64_t* trace,
-                       int32_t trace_cap, cudaStream_t st) {
+                       int32_t trace_cap, bool early, cudaStream_t st) {
   ClusterParams p = params_of(plan);
   p.trace = trace;
   p.trace_cap = trace ? trace_cap : 0;
   SingleJob job;
   job.d = d;
   job.phases_out = phases_out;
+  job.early_ok = early ? 1 : 0;
   void* args[] = {&p, &job};
-  return launch_plan(plan, args, st);
+  return launch_plan(plan, args, st, true);
 }
 
 SolveDesc make_desc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, int plain) {

@@ -329,8 +329,82 @@ def test_host_result_entry_point(dj, orc):
     assert_same((d, p), orc.dijkstra(W, 42), "host buffers")
     # upload a modified matrix into the same graph and solve again
     W2 = W.copy()
-    W2[42, :] = np.where(W2[42, :] == P.INF, P.INF, 1)
+    W2[42, :] = np.where(W2[42, :] == P.INF, P.INF, 1)  # the graph is undirected: keep it symmetric
+    W2[:, 42] = W2[42, :]
     W2[42, 42] = 0
     dj.dj_graph_upload(G, W2)
     d, p = dj.dj_sssp_host(G, 42)
     assert_same((d, p), orc.dijkstra(W2, 42), "after upload")
+
+
+def test_back_to_back_small_solves_keep_stream_order(dj, orc):
+    """Small-graph solves start while the previous kernel on the stream is still running (they
+    are programmatic dependents) and wait for it only before writing their results.  Back to back
+    on one stream: solves into separate buffers each equal the oracle; solves into one shared
+    buffer pair leave the last solve's result; a copy taken by an ordinary kernel between two
+    solves sees the earlier solve's result complete, never a mix."""
+    import torch
+    e = graphgen.bernoulli(1024, 0.1, 1, 100, seed=61)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    srcs = [int(x) for x in graphgen.sources(e.n, 24, 62)]
+    Dr, Prr, _ = orc.dijkstra_many_threads(W, np.array(srcs, dtype=np.int32))
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        D = torch.full((len(srcs), e.n), -5, dtype=torch.int32, device="cuda")
+        Pr = torch.full((len(srcs), e.n), -5, dtype=torch.int32, device="cuda")
+        for i, s in enumerate(srcs):
+            dj.dj_sssp(G, s, D[i], Pr[i], st)
+        d1 = torch.full((e.n,), -5, dtype=torch.int32, device="cuda")
+        p1 = torch.full((e.n,), -5, dtype=torch.int32, device="cuda")
+        snaps = []
+        for s in srcs:
+            dj.dj_sssp(G, s, d1, p1, st)
+            snaps.append((d1.clone(), p1.clone()))  # ordinary kernels between the solves
+    dj.dj_sync(st)
+    for i in range(len(srcs)):
+        assert_same((D[i].cpu().numpy(), Pr[i].cpu().numpy()), (Dr[i], Prr[i]), f"separate buffers #{i}")
+        assert_same((snaps[i][0].cpu().numpy(), snaps[i][1].cpu().numpy()), (Dr[i], Prr[i]), f"snapshot #{i}")
+    assert_same((d1.cpu().numpy(), p1.cpu().numpy()), (Dr[-1], Prr[-1]), "shared buffers")
+    G.free()
+
+
+def test_back_to_back_grid_solves_and_upload(dj, orc):
+    """Grid-engine solves launched back to back (each a programmatic dependent of the previous
+    kernel, sharing the stream's workspace), then a matrix upload followed at once by solves on
+    both engines: every result equals the oracle on the matrix in force when it was enqueued."""
+    import torch
+    e = graphgen.bernoulli(4096, 0.3, 1, 50, seed=63)
+    G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+    W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+    srcs = [int(x) for x in graphgen.sources(e.n, 6, 64)]
+    st = torch.cuda.Stream()
+    D = torch.full((len(srcs), e.n), -5, dtype=torch.int32, device="cuda")
+    Pr = torch.full((len(srcs), e.n), -5, dtype=torch.int32, device="cuda")
+    for i, s in enumerate(srcs):
+        dj.dj_sssp(G, s, D[i], Pr[i], st)
+    dj.dj_sync(st)
+    Dr, Prr, _ = orc.dijkstra_many_threads(W, np.array(srcs, dtype=np.int32))
+    for i in range(len(srcs)):
+        assert_same((D[i].cpu().numpy(), Pr[i].cpu().numpy()), (Dr[i], Prr[i]), f"grid b2b #{i}")
+    # a small graph: upload a changed matrix, then solve right away on the same stream
+    e2 = graphgen.bernoulli(1500, 0.1, 1, 100, seed=65)
+    G2 = dj.dj_load_edges(e2.n, e2.src, e2.dst, e2.w, False)
+    W2 = orc.build_matrix(e2.n, e2.src, e2.dst, e2.w, False)
+    W3 = W2.copy()
+    W3[:7, :] = np.where(W3[:7, :] == P.INF, P.INF, 1)  # edges at nodes 0..6 get weight 1 (kept symmetric)
+    W3[:, :7] = W3[:7, :].T
+    np.fill_diagonal(W3, 0)
+    Wh = torch.from_numpy(W3).pin_memory()
+    d = torch.full((e2.n,), -5, dtype=torch.int32, device="cuda")
+    p = torch.full((e2.n,), -5, dtype=torch.int32, device="cuda")
+    dj.dj_sssp(G2, 3, d, p, st)  # on the old matrix
+    dj.dj_graph_upload(G2, Wh, st)
+    d2 = torch.full((e2.n,), -5, dtype=torch.int32, device="cuda")
+    p2 = torch.full((e2.n,), -5, dtype=torch.int32, device="cuda")
+    dj.dj_sssp(G2, 3, d2, p2, st)  # on the new one
+    dj.dj_sync(st)
+    assert_same((d.cpu().numpy(), p.cpu().numpy()), orc.dijkstra(W2, 3), "before upload")
+    assert_same((d2.cpu().numpy(), p2.cpu().numpy()), orc.dijkstra(W3, 3), "after upload")
+    G.free()
+    G2.free()
