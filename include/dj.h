@@ -177,7 +177,14 @@ typedef struct dj_solve_opts {
                              row per CTA streams HBM faster than every CTA reading its slice of
                              every row).  0 = auto (n/8 clamped to 512..2048, on graphs with at
                              least n^2/32 finite entries; never on sparser ones), -1 = never. */
-  int32_t reserved[3];
+  int32_t rowpush;        /* grid engine, graphs with fewer than n^2/32 finite entries: a phase with at
+                             least this many candidates (while a sixteenth of the nodes stays
+                             unsettled) reads its settled rows whole, in 2048-column pieces spread over
+                             every warp of the grid, and pushes each finite entry into per-column keys
+                             that the owners commit from after one more grid barrier.  0 = auto (four
+                             candidates per CTA), -1 = never; also forced (> 0) on dense graphs when
+                             rowsplit is -1. */
+  int32_t reserved[2];
 } dj_solve_opts;
 
 #define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only */

@@ -1152,6 +1152,118 @@ __device__ __forceinline__ bool relax_rows(const Get& get, int total, int b, int
   return ok;
 }
 
+// Row-push relaxation (grid engine, phases of graphs that are not dense).
+// Work items are (candidate k, column chunk c) pairs, k < total, chunks of
+// kPushChunk columns; item it = k * chunks + c goes to warp it mod (G * warps)
+// of the grid, so one settled row's chunks are read side by side by the warps
+// of one CTA.  A warp skips a candidate that is not settled; otherwise every
+// lane loads its 16-byte pieces of the chunk (kPushLoads in flight) and pushes
+// each finite entry w into gkey[v] as the 64-bit key ((dist[u] + w) << 32) |
+// tie word with atomicMin, so that after a grid barrier gkey[v] holds the
+// smallest (candidate, dist[u] - m, u) any settled row offers v -- the key the
+// other paths reduce per column -- and the owners commit from it.  Rows are
+// read whole and contiguously: large coalesced requests instead of every
+// CTA's narrow slice of every row.  No barrier inside.
+constexpr int kPushChunk = 2048;  // columns per work item (8 KB)
+constexpr int kPushLoads = 16;    // 16-byte loads in flight per lane (one round per item)
+
+// The settled entries among candidates [begin, end) of get(i), as tie words
+// ((dist[u] - m) << bits) | u, into list in candidate order: every CTA derives
+// the same list from the same published candidates (a block-wide scan, no
+// atomics), so work items indexed by list position mean the same row in every
+// CTA.  At most end - begin entries; returns the count; ends synced.
+template <class Get>
+__device__ __forceinline__ int compact_settled(const Get& get, int begin, int end, const Decision& D,
+                                               uint32_t bits_u, uint32_t* list, BlockScratch* sc) {
+  constexpr int K = 4;  // consecutive candidates per thread (loads in flight)
+  const int T = static_cast<int>(blockDim.x), lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  int out = 0;
+  for (int i0 = begin; i0 < end; i0 += K * T) {
+    uint4 e[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int i = i0 + static_cast<int>(threadIdx.x) * K + j;
+      e[j] = i < end ? get(i) : make_uint4(0xffffffffu, kInf, kInf, 0u);
+    }
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (e[j].x != 0xffffffffu && in_settled(e[j].x, e[j].y, e[j].z, D)) {
+        flags |= 1u << j;
+        ++cnt;
+      }
+    uint32_t incl = cnt;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sc->r32[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t wsum = lane < nw ? sc->r32[lane] : 0u;
+      uint32_t wi = wsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      if (lane < nw) sc->r32b[lane] = wi - wsum;  // exclusive prefix of the warps
+      if (lane == 31) sc->b32 = wi;
+    }
+    __syncthreads();
+    uint32_t pos = static_cast<uint32_t>(out) + sc->r32b[warp] + incl - cnt;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if ((flags >> j) & 1u) list[pos++] = ((e[j].y - D.m) << bits_u) | e[j].x;
+    out += static_cast<int>(sc->b32);
+    __syncthreads();  // sc is rewritten by the next round
+  }
+  return out;
+}
+
+// Push the rows of the cnt settled tie words in list (the same list in every
+// CTA) as work items (row k, chunk c) spread over every warp of the grid.
+__device__ __forceinline__ void relax_push(const uint32_t* list, int cnt, int G, const int32_t* __restrict__ W,
+                                           int64_t pitch, const Decision& D, uint32_t bits_u,
+                                           unsigned long long* gkey) {
+  const int lane = threadIdx.x & 31, nw = static_cast<int>(blockDim.x >> 5);
+  const uint32_t umask = (1u << bits_u) - 1u;
+  const int chunks = static_cast<int>((pitch + kPushChunk - 1) / kPushChunk);
+  const int64_t items = static_cast<int64_t>(cnt) * chunks;
+  const int64_t stride = static_cast<int64_t>(G) * nw;
+  for (int64_t it = static_cast<int64_t>(blockIdx.x) * nw + (threadIdx.x >> 5); it < items; it += stride) {
+    const int k = static_cast<int>(it / chunks);
+    const int c = static_cast<int>(it - static_cast<int64_t>(k) * chunks);
+    const uint32_t tb32 = list[k];
+    const uint32_t u = tb32 & umask;
+    const uint32_t du = D.m + (tb32 >> bits_u);
+    const uint64_t tb = static_cast<uint64_t>(tb32);
+    const int64_t col0 = static_cast<int64_t>(c) * kPushChunk;
+    const int nv = static_cast<int>(min(static_cast<int64_t>(kPushChunk), pitch - col0) / 4);
+    const int32_t* row = W + static_cast<int64_t>(u) * pitch + col0;
+    for (int v0 = 0; v0 < nv; v0 += 32 * kPushLoads) {
+      int4 x[kPushLoads];
+#pragma unroll
+      for (int r = 0; r < kPushLoads; ++r) {
+        const int iv = v0 + 32 * r + lane;
+        x[r] = iv < nv ? ld_stream16(row + 4 * iv) : make_int4(int(kInf), int(kInf), int(kInf), int(kInf));
+      }
+#pragma unroll
+      for (int r = 0; r < kPushLoads; ++r) {
+        const uint32_t w4[4] = {static_cast<uint32_t>(x[r].x), static_cast<uint32_t>(x[r].y),
+                                static_cast<uint32_t>(x[r].z), static_cast<uint32_t>(x[r].w)};
+        if ((w4[0] & w4[1] & w4[2] & w4[3]) == kInf) continue;  // all four INF (entries are <= INF)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (w4[q] < kInf)
+            atomicMin(gkey + col0 + 4 * (v0 + 32 * r + lane) + q,
+                      (static_cast<unsigned long long>(du + w4[q]) << 32) | tb);
+      }
+    }
+  }
+}
+
 // Snapshot word of column j for relax_rows: dist, with the top bit set when
 // a tie can still replace pred (IN bound on, pred's dist >= this phase's m).
 __device__ __forceinline__ uint32_t snapshot_word(const Slice& s, int j, const Decision& D) {

@@ -61,6 +61,7 @@ struct GridParams {
   int32_t list_cap;    // staged settled rows per segment (column-filtered relaxation)
   int32_t gather_max;  // load only the live columns when at most this many groups are live (-1: never filter)
   int32_t rs_min;      // row-split relaxation for phases with at least this many candidates (0: never)
+  int32_t rp_min;      // row-push relaxation (graphs that are not dense) from this many candidates (0: never)
   int32_t ring_bytes;  // bytes of the ring region (also the row-split buffers)
   uint32_t* gsnap;     // [pitch] column snapshots at the start of a row-split phase
   unsigned long long* gkey;  // [2][pitch] merged row-split keys per phase parity, all ones between uses
@@ -175,7 +176,7 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
 
   uint32_t* bar = p.ctl + kCtlBarrier;
   uint32_t* abort_flag = p.ctl + kCtlAbort;
-  if (p.rs_min > 0) {  // row-split merge keys of this slice, ordered before use by the first barrier
+  if (p.gkey) {  // row-split / row-push merge keys of this slice, ordered before use by the first barrier
     for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
       p.gkey[s.c0 + j] = ~0ull;
       p.gkey[static_cast<size_t>(p.pitch) + s.c0 + j] = ~0ull;
@@ -194,11 +195,12 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     uint64_t key;
     uint32_t Lc;
     uint32_t unvis = 0;
+    const bool packed = p.rs_min > 0 || p.rp_min > 0;
     const int c = publish_partial(s, p.span, p.plain != 0, p.use_in != 0, part, out, &sc, &key, &Lc,
-                                  p.rs_min > 0 ? &unvis : nullptr);
-    // with row split on (slices < 2^16 columns): count | (unvisited non-candidates << 16)
-    const uint32_t w4 = p.rs_min > 0 ? static_cast<uint32_t>(c) | ((unvis - static_cast<uint32_t>(c)) << 16)
-                                     : static_cast<uint32_t>(c);
+                                  packed ? &unvis : nullptr);
+    // with row split or row push on (slices < 2^16 columns): count | (unvisited non-candidates << 16)
+    const uint32_t w4 = packed ? static_cast<uint32_t>(c) | ((unvis - static_cast<uint32_t>(c)) << 16)
+                               : static_cast<uint32_t>(c);
     if (threadIdx.x == 0)
       p.partials[static_cast<size_t>(phase & 1) * G + b] =
           make_uint4(static_cast<uint32_t>(key), static_cast<uint32_t>(key >> 32), Lc, w4);
@@ -226,9 +228,9 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
         k = kk < k ? kk : k;
         l = min(l, x.z);
         if (i0 + r < i1) s_off[i0 + r] = sum;
-        const uint32_t cnt = p.rs_min > 0 ? (x.w & 0xFFFFu) : x.w;
+        const uint32_t cnt = packed ? (x.w & 0xFFFFu) : x.w;
         sum += cnt;
-        rem += p.rs_min > 0 ? (x.w >> 16) : 0u;
+        rem += packed ? (x.w >> 16) : 0u;
       }
       uint32_t incl = sum;
 #pragma unroll
@@ -270,12 +272,16 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     // row split for a big phase after which a fair share of the nodes stays unsettled (otherwise
     // few columns are live and the filtered paths read less); the same decision in every CTA
     const bool rowsplit = p.rs_min > 0 && !p.plain && total >= p.rs_min && 16ull * s_rem >= static_cast<uint64_t>(p.n);
+    // row push (graphs that are not dense): phases with enough candidates to occupy the grid's
+    // warps, while a fair share of the nodes stays unsettled (otherwise the filtered paths read less)
+    const bool rowpush = !rowsplit && p.rp_min > 0 && !p.plain && total >= p.rp_min &&
+                         16ull * s_rem >= static_cast<uint64_t>(p.n);
     // the gather's column pass: on undirected graphs (measured: it costs the sparse directed graph
     // more than it saves), for phases with enough settled rows to pay for it, the whole list in one
     // segment, room for its table and lists
     const bool colpass = !p.plain && p.sym && total >= kColPassMin && total <= p.list_cap &&
                          p.ring_bytes / 4 >= static_cast<int>(p.pitch / 2) + 2 * s.sw;
-    const int nlg = rowsplit           ? 0
+    const int nlg = (rowsplit || rowpush) ? 0
                     : p.gather_max >= 0 ? live_groups(s, D, p.bits_u, glist, gthr, &sc, colpass && p.ts.cap > 0,
                                                       colpass && p.sym != 0)
                                         : s.nvec;
@@ -285,8 +291,25 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
         p.gather_max >= 0 &&
         (nlg <= p.gather_max ||
          (colpass && static_cast<int>(sc.cnt[26]) + max(0, static_cast<int>(sc.cnt[25]) - kMaxRowColumns) <= p.gather_max));
-    if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(rowsplit ? 0xFFFFu : nlg) << 32;
-    if (rowsplit) {
+    if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(rowsplit ? 0xFFFFu : rowpush ? 0xFFFEu : nlg) << 32;
+    if (rowpush) {
+      unsigned long long* gk = p.gkey + static_cast<size_t>(phase & 1) * p.pitch;
+      for (int seg = 0; seg < total; seg += p.list_cap) {  // the same segments and lists in every CTA
+        const int cnt = compact_settled(get, seg, min(total, seg + p.list_cap), D, p.bits_u, list, &sc);
+        relax_push(list, cnt, G, p.W, p.pitch, D, p.bits_u, gk);
+        __syncthreads();  // the list is rewritten by the next segment
+      }
+      // every CTA's pushes are in gkey before the owners read their slices
+      if (!grid_barrier(bar, ++nbar * static_cast<uint32_t>(G), abort_flag, p.words, p.timeout_ns, &s_flag))
+        return;
+      for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+        bkey[j] = __ldcg(gk + s.c0 + j);
+        gk[s.c0 + j] = ~0ull;  // reused two phases later, after at least one more barrier
+      }
+      __syncthreads();
+      if (tr && threadIdx.x == 0) tr[5] = global_ns();
+      commit_keys(s, D, p.bits_u, bkey, part);
+    } else if (rowsplit) {
       unsigned long long* gk = p.gkey + static_cast<size_t>(phase & 1) * p.pitch;
       // this slice's snapshot for the other CTAs' merges, announced without waiting
       for (int j = threadIdx.x; j < s.sw; j += blockDim.x) p.gsnap[s.c0 + j] = snapshot_word(s, j, D);
@@ -887,8 +910,16 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   const int rs_min = (!want_rs || L.rs_bytes == 0 || L.swcap > L.list_cap || L.swcap >= 65536) ? 0
                      : o.rowsplit > 0                                                         ? o.rowsplit
                                                                                               : auto_rowsplit_min(g->n);
+  // row push on graphs that are not dense (or forced while the row split is off); packed partial
+  // counts need slices below 2^16 columns
+  // (auto: phases of at least 4 candidates per CTA; measured on the sparse directed n = 32768
+  // graph: 2298 us per solve without, 2244 from G, 2220 from 2 G, 2200 from 4 G candidates)
+  const int rp_min = (o.mode == DJ_MODE_PLAIN || o.rowpush < 0 || rs_min > 0 || L.swcap >= 65536) ? 0
+                     : o.rowpush > 0                                                       ? o.rowpush
+                     : !dense                                                              ? 4 * G
+                                                                                           : 0;
   const size_t snap_bytes = rs_min > 0 ? static_cast<size_t>(g->pitch) * 4 : 0;  // pitch is a multiple of 4
-  const size_t gkey_bytes = rs_min > 0 ? static_cast<size_t>(2) * g->pitch * 8 : 0;
+  const size_t gkey_bytes = (rs_min > 0 || rp_min > 0) ? static_cast<size_t>(2) * g->pitch * 8 : 0;
   // the stream's kept workspace (its control words are zero between launches: see grid_exit),
   // or one allocated for this call
   const size_t ws_bytes = ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes;
@@ -934,10 +965,12 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                  : o.live > 0                                              ? std::min(o.live, kGridThreads)
                                                                            : auto_gather_max(nvec_cta);
   p.rs_min = rs_min;
+  p.rp_min = rp_min;
   p.ring_bytes = static_cast<int32_t>(ring_region(L, nwarps));
   p.gsnap = rs_min > 0 ? reinterpret_cast<uint32_t*>(ws + ctl_bytes + part_bytes + cand_bytes) : nullptr;
-  p.gkey = rs_min > 0 ? reinterpret_cast<unsigned long long*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes)
-                      : nullptr;
+  p.gkey = (rs_min > 0 || rp_min > 0)
+               ? reinterpret_cast<unsigned long long*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes)
+               : nullptr;
   p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
   void* args[] = {&p};
@@ -1288,7 +1321,8 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.trace = nullptr;
   p.list_cap = L.list_cap;
   p.gather_max = auto_gather_max(nvec_cta);
-  p.rs_min = 0;  // no row-split state in the fixed scratch
+  p.rs_min = 0;  // no row-split or row-push state in the fixed scratch
+  p.rp_min = 0;
   p.ring_bytes = static_cast<int32_t>(ring_region(L, nwarps));
   p.gsnap = nullptr;
   p.gkey = nullptr;

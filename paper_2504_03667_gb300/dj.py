@@ -56,8 +56,8 @@ class dj_solve_opts(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("debug_skip_cta", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("trace", ctypes.c_void_p), ("settle", ctypes.c_int32),
-                ("live", ctypes.c_int32), ("rowsplit", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("live", ctypes.c_int32), ("rowsplit", ctypes.c_int32), ("rowpush", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class dj_batch_opts(ctypes.Structure):
@@ -291,10 +291,11 @@ def dj_graph_free(g):
 
 def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, threads=0, ctas_per_sm=0,
                     unroll=0, timeout_ns=0, debug_skip_cta=-1, trace=None, settle=0, live=0,
-                    rowsplit=0) -> dj_solve_opts:
-    """trace: optional int64 CUDA tensor receiving the grid engine's per-phase timeline.
+                    rowsplit=0, rowpush=0) -> dj_solve_opts:
+    """trace: optional int64 CUDA tensor receiving the per-phase timeline.
     live: grid engine column filter (0 auto, -1 off, > 0 gather threshold in 4-column groups).
-    rowsplit: grid engine row-split phases (0 auto, -1 off, > 0 minimum settled candidates)."""
+    rowsplit: grid engine row-split phases (0 auto, -1 off, > 0 minimum settled candidates).
+    rowpush: grid engine row-push phases (0 auto on sparse graphs, -1 off, > 0 minimum candidates)."""
     o = dj_solve_opts()
     load_library().dj_solve_opts_init(ctypes.byref(o))
     o.mode, o.engine, o.cluster_size, o.threads = mode, engine, cluster_size, threads
@@ -304,6 +305,7 @@ def make_solve_opts(mode=DJ_MODE_AUTO, engine=DJ_ENGINE_AUTO, cluster_size=0, th
     o.settle = settle
     o.live = live
     o.rowsplit = rowsplit
+    o.rowpush = rowpush
     return o
 
 

@@ -30,13 +30,13 @@ def dj():
     return _dj
 
 
-def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0, rowsplit=0):
+def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0, rowsplit=0, rowpush=0):
     import torch
     n = dj.dj_graph_get_info(g)["n"]
     dist = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     pred = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     dj.dj_sssp_ex(g, s, dist, pred, dj.make_solve_opts(mode=mode, engine=engine, cluster_size=cluster_size,
-                                                       live=live, rowsplit=rowsplit))
+                                                       live=live, rowsplit=rowsplit, rowpush=rowpush))
     dj.dj_sync()
     return dist.cpu().numpy(), pred.cpu().numpy()
 
@@ -157,15 +157,18 @@ def test_complete_equal_weights_and_path(dj, orc):
     assert np.array_equal(d, 3 * np.arange(n)) and np.array_equal(p, np.arange(n) - 1)
 
 
-PATHS = [("ring", -1, -1), ("auto", 0, 0), ("gather", 1 << 20, -1), ("rowsplit", -1, 1)]
+PATHS = [("ring", -1, -1, -1), ("auto", 0, 0, 0), ("gather", 1 << 20, -1, -1), ("rowsplit", -1, 1, -1),
+         ("rowpush", -1, -1, 1)]
 
 
-@pytest.mark.parametrize("live,rowsplit", [(lv, rs) for _, lv, rs in PATHS], ids=[n for n, _, _ in PATHS])
-def test_relaxation_paths(dj, orc, live, rowsplit):
+@pytest.mark.parametrize("live,rowsplit,rowpush", [(lv, rs, rp) for _, lv, rs, rp in PATHS],
+                         ids=[n for n, _, _, _ in PATHS])
+def test_relaxation_paths(dj, orc, live, rowsplit, rowpush):
     """Grid engine relaxation paths: streaming every settled row's slice (ring), the default (skip a
-    slice with no live column, load only the live groups when few, row split for big phases),
-    loading only the live groups in every phase (gather), and row split in every phase all give
-    Algorithm 1's dist and pred.  Dense graphs with weights 1..3 make ties on both dist and pred
+    slice with no live column, load only the live groups when few, row split for big phases of
+    dense graphs, row push for those of sparser ones), loading only the live groups in every phase
+    (gather), row split in every phase and row push in every phase all give Algorithm 1's dist
+    and pred.  Dense graphs with weights 1..3 make ties on both dist and pred
     pervasive; zero weights turn the IN bound off; narrow weight ranges give columns a few
     dozen rows of their minimum in-weight, the tie sources the gather path settles tie-only
     columns from."""
@@ -186,8 +189,8 @@ def test_relaxation_paths(dj, orc, live, rowsplit):
             for mode in modes:
                 if mode == 2 and s != 0:
                     continue
-                assert_same(solve(dj, G, s, engine=1, mode=mode, live=live, rowsplit=rowsplit), ref,
-                            f"{what} s={s} mode={mode}")
+                assert_same(solve(dj, G, s, engine=1, mode=mode, live=live, rowsplit=rowsplit, rowpush=rowpush),
+                            ref, f"{what} s={s} mode={mode}")
         G.free()
 
 
@@ -213,7 +216,9 @@ def test_sparse_directed_n32768_full(dj, orc):
     G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
     W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
     ref = orc.dijkstra(W, s)
-    assert_same(solve(dj, G, s), ref, "n=32768 directed")
+    assert_same(solve(dj, G, s), ref, "n=32768 directed")  # the launch the benchmark times
+    assert_same(solve(dj, G, s, engine=1, rowpush=-1), ref, "n=32768 directed, row push off")
+    assert_same(solve(dj, G, s, engine=1, rowpush=1), ref, "n=32768 directed, row push in every phase")
     assert_same(solve(dj, G, s, engine=2, cluster_size=16), ref, "n=32768 directed, cluster engine")
 
 
