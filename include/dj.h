@@ -272,10 +272,12 @@ int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* p
 int dj_sssp_lc(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
 
 /* ------------------------------------------------------------------ batched solves */
-/* k solves (graph[i], sources[i]) in ONE persistent launch: one thread-block
+/* k solves (graph[i], sources[i]) in one persistent launch: one thread-block
  * cluster per solve at a time, solves pulled from a device queue (largest n
- * first), graphs of different n allowed.  Rows shared by concurrent solves of
- * one graph are reused through L2.  Each solve's result equals dj_sssp's.
+ * first), graphs of different n allowed, rows shared by concurrent solves of
+ * one graph reused through L2; or, for solves of one graph whose shape the
+ * autotuner found faster that way, the lockstep engine
+ * (DJ_BATCH_ENGINE_LOCKSTEP).  Each solve's result equals dj_sssp's.
  *   graphs   HOST array of k graph handles (all on the current device)
  *   sources  HOST array of k int32
  *   dist, pred  HOST arrays of k DEVICE pointers, n_i int32 each
@@ -290,8 +292,22 @@ typedef struct dj_batch_opts {
   int32_t clusters;      /* clusters resident at once, 0 = as many as fit */
   int32_t settle;        /* DJ_SETTLE_* (defined below), 0 = auto */
   int32_t copies;        /* DJ_COPIES_*: how a CTA's ring copies its slice of a settled row */
-  int32_t reserved[6];
+  int32_t engine;        /* DJ_BATCH_ENGINE_*: which engine runs the batch */
+  int32_t reserved[5];
 } dj_batch_opts;
+
+#define DJ_BATCH_ENGINE_AUTO 0     /* the tuned engine for this graph shape if there is one, else clusters */
+#define DJ_BATCH_ENGINE_CLUSTER 1  /* one thread-block cluster per solve, solves pulled from a device queue */
+#define DJ_BATCH_ENGINE_LOCKSTEP 2 /* every solve of ONE graph advances phase by phase together over every
+                                      SM, so a row a phase needs is read once for all the sources that
+                                      settle it (per-source results as Algorithm 1's).  The graph keeps
+                                      a column-tiled copy of its matrix (about the matrix's size, counted
+                                      in dj_graph_info.bytes) until it is freed.  Sources are taken in
+                                      groups of at most 256 (fewer for n > 8192; DJ_EUNSUPPORTED where
+                                      fewer than 32 fit, roughly n > 13000), one cooperative launch per
+                                      group.  Fewer HBM bytes, but bound by instruction issue: slower
+                                      than clusters on the shapes measured, so only chosen explicitly or
+                                      by the autotuner. */
 
 #define DJ_COPIES_AUTO 0   /* wide where the slice allows it */
 #define DJ_COPIES_NARROW 1 /* every warp copies its own 512-byte part of each row */
@@ -313,13 +329,32 @@ int dj_batch_create(const dj_graph* const* graphs, const int32_t* sources, int32
 int dj_batch_launch(dj_batch* b, uint64_t stream);
 int dj_batch_free(dj_batch* b); /* caller synchronises first */
 
-/* Autotuner: times every supported (cluster size, threads) pair for this
- * batch on the device and stores the fastest in the batch (and in the
- * process-wide table keyed by (n bucket, density bucket, SM count), which
- * DJ_MODE_AUTO batches consult).  Synchronous; overwrites the batch's outputs.
- * Reports the choice through the optional out-parameters. */
+/* Autotuner: times every supported cluster size (2, 4, 8, 16) and, for
+ * solves of one graph, the lockstep engine, on the device, and keeps the
+ * fastest for the batch and in the process-wide table keyed by (n bucket =
+ * floor(log2 n), density bucket = floor(log2(n^2 / finite entries)) capped at
+ * 20, SM count), which later batches of one graph consult.  When the
+ * environment variable DJ_TUNE_FILE names a file, the table is read from it on
+ * first use and written back after every autotune, so another process picks up
+ * the choice.  Synchronous; overwrites the batch's outputs.  Reports the choice
+ * (cluster_size 0 for the lockstep engine) through the optional out-parameters. */
 int dj_batch_autotune(dj_batch* b, uint64_t stream, int32_t* cluster_size, int32_t* threads,
                       float* best_ms);
+
+/* The engine a prepared batch launches (DJ_BATCH_ENGINE_CLUSTER or _LOCKSTEP). */
+int dj_batch_get_engine(const dj_batch* b, int32_t* engine);
+
+/* The autotuner's table as JSON (host only, no GPU needed):
+ *   {"version": 1, "entries": [{"n_bucket": 13, "density_bucket": 4, "sms": 152,
+ *     "engine": "lockstep", "cluster_size": 0, "threads": 512, "ms": 3.1}, ...]}
+ * dj_tune_load merges a file's entries into the table (DJ_EINVAL if it cannot
+ * be read); dj_tune_save writes the table (atomically, through a temporary
+ * file); dj_tune_lookup returns the entry for a graph of n nodes with
+ * `entries` finite off-diagonal entries on a device of num_sms SMs (DJ_EINVAL
+ * if none).  engine: DJ_BATCH_ENGINE_*. */
+int dj_tune_load(const char* path);
+int dj_tune_save(const char* path);
+int dj_tune_lookup(int32_t n, uint64_t entries, int32_t num_sms, int32_t* engine, int32_t* cluster_size);
 
 /* ------------------------------------------------------------------ serving */
 typedef struct dj_server dj_server;

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdj.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dj_load.cu", "dj_solve.cu", "dj_api.cu", "dj_serve.cu", "dj_lc.cu", "dj_csr.cu"]
+SOURCES = ["dj_load.cu", "dj_solve.cu", "dj_api.cu", "dj_serve.cu", "dj_lc.cu", "dj_csr.cu", "dj_lockstep.cu"]
 HEADERS = ["dj_common.cuh", "dj_core.cuh", "dj_internal.h", "dj_noalloc_size.h"]
 
 

@@ -2,7 +2,9 @@
 // batched solves.  Every entry point validates its arguments on the host and
 // only then enqueues device work.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -254,23 +256,186 @@ struct dj_batch {
   ClusterLaunch cl;
   ClusterPlan plan;
   bool tuned = false;
+  // lockstep engine (every solve on one graph)
+  dj_graph* graph = nullptr;   // the shared graph, or nullptr
+  bool lockstep = false;       // launches run the lockstep engine
+  bool ls_ok = false;          // the lockstep engine can run this batch
+  LockstepPlan ls;
+  LsSource* ls_src = nullptr;  // device: the k sources in the caller's order
+  uint8_t* ls_ws = nullptr;    // device workspace (first 256 bytes zero between launches)
+  int ls_use_in = 1;
+  bool ls_possible = false;    // one graph, phase mode: the autotuner may try the lockstep engine
+  std::vector<LsSource> ls_host;
 };
 
-// Autotuned choices per (n bucket, density bucket, SM count), process-wide.
+// ---- autotuned choices per (n bucket, density bucket, SM count), process-wide, optionally
+// kept in a JSON file (DJ_TUNE_FILE, or dj_tune_load / dj_tune_save)
 struct TuneKey {
   int nb, db, sms;
   bool operator==(const TuneKey& o) const { return nb == o.nb && db == o.db && sms == o.sms; }
 };
 struct TuneVal {
+  int engine;  // DJ_BATCH_ENGINE_CLUSTER or DJ_BATCH_ENGINE_LOCKSTEP
   int cluster_size, threads;
+  double ms;
 };
 static std::mutex g_tune_mu;
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+static bool g_tune_env_loaded = false;
 
 static int n_bucket(int32_t n) {
   int b = 0;
   while ((1 << (b + 1)) <= n && b < 30) ++b;
   return b;
+}
+// floor(log2(n^2 / finite entries)), at most 20: 0 for complete graphs, 1 at density 1/2, 4 at 1/20
+static int density_bucket(int32_t n, uint64_t entries) {
+  const double ratio = static_cast<double>(n) * static_cast<double>(n) / static_cast<double>(std::max<uint64_t>(entries, 1));
+  int b = 0;
+  while (b < 20 && std::ldexp(1.0, b + 1) <= ratio) ++b;
+  return b;
+}
+static TuneKey tune_key(int32_t n, uint64_t entries, int sms) { return TuneKey{n_bucket(n), density_bucket(n, entries), sms}; }
+
+static int tune_load_locked(const char* path);
+static void tune_env_load_locked() {
+  if (g_tune_env_loaded) return;
+  g_tune_env_loaded = true;
+  const char* f = std::getenv("DJ_TUNE_FILE");
+  if (f && *f) {
+    tune_load_locked(f);
+    clear_error();
+  }
+}
+static bool tune_find(const TuneKey& key, TuneVal* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_env_load_locked();
+  for (auto& kv : g_tune)
+    if (kv.first == key) {
+      *out = kv.second;
+      return true;
+    }
+  return false;
+}
+static void tune_put_locked(const TuneKey& key, const TuneVal& v) {
+  for (auto& kv : g_tune)
+    if (kv.first == key) {
+      kv.second = v;
+      return;
+    }
+  g_tune.push_back({key, v});
+}
+
+// The table as JSON: {"version": 1, "entries": [{"n_bucket": .., "density_bucket": .., "sms": ..,
+// "engine": "cluster"|"lockstep", "cluster_size": .., "threads": .., "ms": ..}, ...]}
+static int tune_save_locked(const char* path) {
+  std::string out = "{\"version\": 1, \"entries\": [";
+  for (size_t i = 0; i < g_tune.size(); ++i) {
+    const auto& k = g_tune[i].first;
+    const auto& v = g_tune[i].second;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf),
+                  "%s\n  {\"n_bucket\": %d, \"density_bucket\": %d, \"sms\": %d, \"engine\": \"%s\", "
+                  "\"cluster_size\": %d, \"threads\": %d, \"ms\": %.6g}",
+                  i ? "," : "", k.nb, k.db, k.sms, v.engine == DJ_BATCH_ENGINE_LOCKSTEP ? "lockstep" : "cluster",
+                  v.cluster_size, v.threads, v.ms);
+    out += buf;
+  }
+  out += "\n]}\n";
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return set_error(DJ_EINVAL, std::string("cannot write ") + tmp);
+  const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
+  std::fclose(f);
+  if (!ok || std::rename(tmp.c_str(), path) != 0) return set_error(DJ_EINVAL, std::string("cannot write ") + path);
+  return DJ_OK;
+}
+
+// Minimal reader for the format above: every {...} object inside "entries" with integer fields
+// and an "engine" string.  Entries with missing fields are skipped; later entries of a key win.
+static bool json_int(const std::string& obj, const char* name, long* out) {
+  const std::string key = std::string("\"") + name + "\"";
+  size_t p = obj.find(key);
+  if (p == std::string::npos) return false;
+  p = obj.find(':', p + key.size());
+  if (p == std::string::npos) return false;
+  char* end = nullptr;
+  const long v = std::strtol(obj.c_str() + p + 1, &end, 10);
+  if (end == obj.c_str() + p + 1) return false;
+  *out = v;
+  return true;
+}
+static bool json_num(const std::string& obj, const char* name, double* out) {
+  const std::string key = std::string("\"") + name + "\"";
+  size_t p = obj.find(key);
+  if (p == std::string::npos) return false;
+  p = obj.find(':', p + key.size());
+  if (p == std::string::npos) return false;
+  char* end = nullptr;
+  const double v = std::strtod(obj.c_str() + p + 1, &end);
+  if (end == obj.c_str() + p + 1) return false;
+  *out = v;
+  return true;
+}
+static int tune_load_locked(const char* path) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return set_error(DJ_EINVAL, std::string("cannot read ") + path);
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  size_t p = text.find("\"entries\"");
+  if (p == std::string::npos) return set_error(DJ_EINVAL, std::string("no \"entries\" in ") + path);
+  p = text.find('[', p);
+  int loaded = 0;
+  while (p != std::string::npos) {
+    const size_t a = text.find('{', p);
+    const size_t close = text.find(']', p);
+    if (a == std::string::npos || (close != std::string::npos && close < a)) break;
+    const size_t z = text.find('}', a);
+    if (z == std::string::npos) break;
+    const std::string obj = text.substr(a, z - a + 1);
+    p = z + 1;
+    long nb, db, sms, cs = 0, th = 0;
+    double ms = 0.0;
+    if (!json_int(obj, "n_bucket", &nb) || !json_int(obj, "density_bucket", &db) || !json_int(obj, "sms", &sms))
+      continue;
+    json_int(obj, "cluster_size", &cs);
+    json_int(obj, "threads", &th);
+    json_num(obj, "ms", &ms);
+    const int engine = obj.find("\"lockstep\"") != std::string::npos ? DJ_BATCH_ENGINE_LOCKSTEP : DJ_BATCH_ENGINE_CLUSTER;
+    if (engine == DJ_BATCH_ENGINE_CLUSTER && (cs < 1 || cs > 16)) continue;
+    tune_put_locked(TuneKey{static_cast<int>(nb), static_cast<int>(db), static_cast<int>(sms)},
+                    TuneVal{engine, static_cast<int>(cs), static_cast<int>(th), ms});
+    ++loaded;
+  }
+  return DJ_OK;
+}
+
+extern "C" int dj_tune_load(const char* path) {
+  clear_error();
+  if (!path) return set_error(DJ_EINVAL, "NULL path");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_env_loaded = true;
+  return tune_load_locked(path);
+}
+
+extern "C" int dj_tune_save(const char* path) {
+  clear_error();
+  if (!path) return set_error(DJ_EINVAL, "NULL path");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return tune_save_locked(path);
+}
+
+extern "C" int dj_tune_lookup(int32_t n, uint64_t entries, int32_t num_sms, int32_t* engine, int32_t* cluster_size) {
+  clear_error();
+  if (n < 1 || num_sms < 1) return set_error(DJ_EINVAL, "need n >= 1 and num_sms >= 1");
+  TuneVal v;
+  if (!tune_find(tune_key(n, entries, num_sms), &v)) return set_error(DJ_EINVAL, "no tuned entry for this key");
+  if (engine) *engine = v.engine;
+  if (cluster_size) *cluster_size = v.cluster_size;
+  return DJ_OK;
 }
 
 static int heuristic_cluster_size(int32_t max_pitch) {
@@ -284,6 +449,48 @@ static int batch_descs(const dj_graph* const* graphs, const int32_t* sources, in
                        int32_t* const* pred, int plain, int device, std::vector<SolveDesc>* h, int32_t* max_n,
                        int32_t* max_pitch);
 
+// The one graph every solve of the batch uses, or nullptr.
+static dj_graph* shared_graph(const dj_graph* const* graphs, int32_t k) {
+  if (k < 1) return nullptr;
+  for (int32_t i = 1; i < k; ++i)
+    if (graphs[i] != graphs[0]) return nullptr;
+  return const_cast<dj_graph*>(graphs[0]);
+}
+
+// Auto never picks the lockstep engine without a tuned entry that does: measured on GB300 it is
+// slower than the cluster engine on every shape tried (256 sources of n = 8192, p = 0.05:
+// 18.7 against 10.1 ms; n = 4096, p = 0.5: 7.9 against 2.4 ms), being bound by instruction
+// issue where the cluster engine is bound by streaming.
+
+static void free_batch(dj_batch* b) {
+  if (!b) return;
+  cudaFree(b->descs);
+  cudaFree(b->ls_src);
+  cudaFree(b->ls_ws);
+  delete b;
+}
+
+// Sizes, source table, workspace and tiled matrix of the lockstep engine for batch b (once).
+static int prepare_lockstep(dj_batch* b) {
+  if (b->ls_ok) return DJ_OK;
+  if (int rc = plan_lockstep(b->graph, b->k, &b->ls)) return rc;
+  const std::vector<LsSource>& hs = b->ls_host;
+  cudaError_t e = cudaMalloc(&b->ls_src, hs.size() * sizeof(LsSource));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(lockstep sources)");
+  e = cudaMemcpy(b->ls_src, hs.data(), hs.size() * sizeof(LsSource), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "lockstep source upload");
+  e = cudaMalloc(&b->ls_ws, b->ls.ws_bytes);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(lockstep workspace)");
+  e = cudaMemset(b->ls_ws, 0, 256);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemset(lockstep workspace)");
+  const int32_t* tiled = nullptr;
+  if (int rc = lockstep_tiles(b->graph, b->ls, nullptr, &tiled)) return rc;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "building the column-tiled matrix");
+  b->ls_ok = true;
+  return DJ_OK;
+}
+
 extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sources, int32_t k,
                                int32_t* const* dist, int32_t* const* pred, const dj_batch_opts* opts, dj_batch** out) {
   clear_error();
@@ -294,6 +501,7 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
   dj_batch_opts_init(&o);
   if (opts) o = *opts;
   if (o.copies < DJ_COPIES_AUTO || o.copies > DJ_COPIES_WIDE) return set_error(DJ_EINVAL, "unknown copies");
+  if (o.engine < DJ_BATCH_ENGINE_AUTO || o.engine > DJ_BATCH_ENGINE_LOCKSTEP) return set_error(DJ_EINVAL, "unknown engine");
   DevCtx* ctx = nullptr;
   if (int rc = get_ctx(&ctx)) return rc;
   std::vector<SolveDesc> h;
@@ -318,50 +526,85 @@ extern "C" int dj_batch_create(const dj_graph* const* graphs, const int32_t* sou
   // the queue words start at zero; every launch's last cluster puts them back (no memset per launch)
   e = cudaMemset(b->queue, 0, 64);
   if (e != cudaSuccess) {
-    cudaFree(b->descs);
-    delete b;
+    free_batch(b);
     return cuda_error(e, "cudaMemset(batch queue)");
   }
   if (k > 0) {
     e = cudaMemcpy(b->descs, h.data(), static_cast<size_t>(k) * sizeof(SolveDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-      cudaFree(b->descs);
-      delete b;
+      free_batch(b);
       return cuda_error(e, "descriptor upload");
     }
   }
+  b->graph = shared_graph(graphs, k);
+  TuneVal tv{};
+  const bool have_tune = b->graph && tune_find(tune_key(b->graph->n, b->graph->entries, ctx->num_sms), &tv);
   b->cl.cluster_size = o.cluster_size > 0 ? o.cluster_size : 0;
   b->cl.threads = 256;
   b->cl.clusters = o.clusters;
   b->cl.copies = o.copies;
-  if (b->cl.cluster_size == 0) {
-    TuneKey key{n_bucket(max_n), 0, ctx->num_sms};
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (auto& kv : g_tune)
-      if (kv.first == key) b->cl.cluster_size = kv.second.cluster_size;
-  }
+  if (b->cl.cluster_size == 0 && have_tune && tv.engine == DJ_BATCH_ENGINE_CLUSTER) b->cl.cluster_size = tv.cluster_size;
   if (b->cl.cluster_size == 0) b->cl.cluster_size = heuristic_cluster_size(max_pitch);
   if (int rc = plan_cluster(b->max_pitch, b->cl, b->k, &b->plan)) {
-    cudaFree(b->descs);
-    delete b;
+    free_batch(b);
     return rc;
   }
+  // the lockstep engine: forced, or auto for enough solves of one graph (a tuned entry decides)
+  const bool want_ls = o.mode != DJ_MODE_PLAIN && b->graph &&
+                       (o.engine == DJ_BATCH_ENGINE_LOCKSTEP ||
+                        (o.engine == DJ_BATCH_ENGINE_AUTO && o.cluster_size == 0 && have_tune &&
+                         tv.engine == DJ_BATCH_ENGINE_LOCKSTEP));
+  b->ls_use_in = o.settle == DJ_SETTLE_OUT ? 0 : 1;
+  b->ls_possible = b->graph && o.mode != DJ_MODE_PLAIN && o.engine != DJ_BATCH_ENGINE_CLUSTER && k > 0;
+  if (o.engine == DJ_BATCH_ENGINE_LOCKSTEP && !b->ls_possible) {
+    free_batch(b);
+    return set_error(DJ_EUNSUPPORTED, "the lockstep engine needs every solve on one graph, in phase mode");
+  }
+  if (b->ls_possible) {
+    b->ls_host.resize(static_cast<size_t>(k));
+    for (int32_t i = 0; i < k; ++i) b->ls_host[i] = LsSource{dist[i], pred[i], sources[i], 0};
+  }
+  if (want_ls) {
+    const int rc = prepare_lockstep(b);
+    if (rc != DJ_OK && o.engine == DJ_BATCH_ENGINE_LOCKSTEP) {
+      free_batch(b);
+      return rc;
+    }
+    if (rc != DJ_OK) clear_error();
+  }
+  b->lockstep = want_ls && b->ls_ok;
   *out = b;
   return DJ_OK;
+}
+
+static int launch_batch(dj_batch* b, cudaStream_t st) {
+  if (b->k == 0) return DJ_OK;
+  if (b->lockstep) {
+    DevCtx* ctx = nullptr;
+    if (int rc = get_ctx(&ctx)) return rc;
+    const int32_t* tiled = nullptr;
+    if (int rc = lockstep_tiles(b->graph, b->ls, st, &tiled)) return rc;
+    return run_lockstep(b->graph, b->ls, tiled, b->ls_src, b->ls_ws, ctx->words, 0, b->ls_use_in, st);
+  }
+  return run_cluster(b->plan, b->descs, b->k, b->queue, st, false);
 }
 
 extern "C" int dj_batch_launch(dj_batch* b, uint64_t stream) {
   clear_error();
   if (!b) return set_error(DJ_EINVAL, "NULL batch");
-  if (b->k == 0) return DJ_OK;
-  return run_cluster(b->plan, b->descs, b->k, b->queue, reinterpret_cast<cudaStream_t>(stream), false);
+  return launch_batch(b, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int dj_batch_free(dj_batch* b) {
   clear_error();
-  if (!b) return DJ_OK;
-  cudaFree(b->descs);
-  delete b;
+  free_batch(b);
+  return DJ_OK;
+}
+
+extern "C" int dj_batch_get_engine(const dj_batch* b, int32_t* engine) {
+  clear_error();
+  if (!b || !engine) return set_error(DJ_EINVAL, "NULL argument");
+  *engine = b->lockstep ? DJ_BATCH_ENGINE_LOCKSTEP : DJ_BATCH_ENGINE_CLUSTER;
   return DJ_OK;
 }
 
@@ -375,9 +618,25 @@ extern "C" int dj_batch_autotune(dj_batch* b, uint64_t stream, int32_t* cluster_
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  auto time_it = [&](float* out_ms) {  // mean of two launches after a warm-up
+    float sum = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      if (launch_batch(b, st) != DJ_OK) return false;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) sum += ms;
+    }
+    *out_ms = sum / 2.f;
+    return true;
+  };
   float best = 1e30f;
+  int best_engine = DJ_BATCH_ENGINE_CLUSTER;
   ClusterLaunch best_cl = b->cl;
   const ClusterLaunch saved = b->cl;
+  b->lockstep = false;
   for (int c : {2, 4, 8, 16}) {
     ClusterLaunch cl = saved;
     cl.cluster_size = c;
@@ -387,48 +646,49 @@ extern "C" int dj_batch_autotune(dj_batch* b, uint64_t stream, int32_t* cluster_
       clear_error();
       continue;
     }
-    float ms_sum = 0.f;
-    bool ok = true;
-    for (int rep = 0; rep < 3 && ok; ++rep) {
-      cudaEventRecord(e0, st);
-      if (dj_batch_launch(b, stream) != DJ_OK) ok = false;
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_sum += ms;  // first run warms up
-    }
-    if (!ok) {
+    float ms = 0.f;
+    if (!time_it(&ms)) {
       clear_error();
       cudaGetLastError();
       continue;
     }
-    const float ms = ms_sum / 2.f;
     if (ms < best) {
       best = ms;
       best_cl = cl;
     }
   }
+  if (b->ls_possible && prepare_lockstep(b) != DJ_OK) clear_error();
+  if (b->ls_ok) {  // the lockstep engine as one more candidate
+    b->lockstep = true;
+    float ms = 0.f;
+    if (time_it(&ms) && ms < best) {
+      best = ms;
+      best_engine = DJ_BATCH_ENGINE_LOCKSTEP;
+    } else {
+      clear_error();
+      cudaGetLastError();
+    }
+    b->lockstep = false;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->cl = best_cl;
   if (int rc = plan_cluster(b->max_pitch, b->cl, b->k, &b->plan)) return rc;
+  b->lockstep = best_engine == DJ_BATCH_ENGINE_LOCKSTEP;
   b->tuned = true;
-  {
-    TuneKey key{n_bucket(b->max_n), 0, ctx->num_sms};
+  if (b->graph) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    bool found = false;
-    for (auto& kv : g_tune)
-      if (kv.first == key) {
-        kv.second = TuneVal{best_cl.cluster_size, best_cl.threads};
-        found = true;
-      }
-    if (!found) g_tune.push_back({key, TuneVal{best_cl.cluster_size, best_cl.threads}});
+    tune_env_load_locked();
+    tune_put_locked(tune_key(b->graph->n, b->graph->entries, ctx->num_sms),
+                    TuneVal{best_engine, best_engine == DJ_BATCH_ENGINE_LOCKSTEP ? 0 : best_cl.cluster_size,
+                            best_engine == DJ_BATCH_ENGINE_LOCKSTEP ? 512 : best_cl.threads, best});
+    const char* f = std::getenv("DJ_TUNE_FILE");
+    if (f && *f) tune_save_locked(f);
   }
-  if (cluster_size) *cluster_size = best_cl.cluster_size;
-  if (threads) *threads = best_cl.threads;
+  if (cluster_size) *cluster_size = best_engine == DJ_BATCH_ENGINE_LOCKSTEP ? 0 : best_cl.cluster_size;
+  if (threads) *threads = best_engine == DJ_BATCH_ENGINE_LOCKSTEP ? 512 : best_cl.threads;
   if (best_ms) *best_ms = best;
-  if (best >= 1e29f) return set_error(DJ_EUNSUPPORTED, "no cluster configuration could run");
+  if (best >= 1e29f) return set_error(DJ_EUNSUPPORTED, "no batch configuration could run");
   return DJ_OK;
 }
 
@@ -464,6 +724,28 @@ extern "C" int dj_sssp_batch(const dj_graph* const* graphs, const int32_t* sourc
   int32_t max_n, max_pitch;
   if (int rc = batch_descs(graphs, sources, k, dist, pred, 0, ctx->device, &h, &max_n, &max_pitch)) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  dj_graph* g1 = shared_graph(graphs, k);
+  TuneVal tv{};
+  const bool have_tune = g1 && tune_find(tune_key(g1->n, g1->entries, ctx->num_sms), &tv);
+  // solves of one graph whose tuned entry chose the lockstep engine
+  LockstepPlan ls;
+  if (g1 && have_tune && tv.engine == DJ_BATCH_ENGINE_LOCKSTEP && plan_lockstep(g1, k, &ls) == DJ_OK) {
+    std::vector<LsSource> hs(static_cast<size_t>(k));
+    for (int32_t i = 0; i < k; ++i) hs[i] = LsSource{dist[i], pred[i], sources[i], 0};
+    const size_t tbytes = (hs.size() * sizeof(LsSource) + 255) & ~size_t(255);
+    uint8_t* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, tbytes + ls.ws_bytes, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(lockstep batch)");
+    cudaMemcpyAsync(ws, hs.data(), hs.size() * sizeof(LsSource), cudaMemcpyHostToDevice, st);  // pageable: staged
+    cudaMemsetAsync(ws + tbytes, 0, 256, st);
+    const int32_t* tiled = nullptr;
+    int rc = lockstep_tiles(g1, ls, st, &tiled);
+    if (rc == DJ_OK)
+      rc = run_lockstep(g1, ls, tiled, reinterpret_cast<LsSource*>(ws), ws + tbytes, ctx->words, 0, 1, st);
+    cudaFreeAsync(ws, st);
+    return rc;
+  }
+  clear_error();
   // stream-ordered table: allocated, filled, used and freed in stream order
   uint8_t* ws = nullptr;
   const size_t tbytes = static_cast<size_t>(k) * sizeof(SolveDesc);
@@ -476,12 +758,7 @@ extern "C" int dj_sssp_batch(const dj_graph* const* graphs, const int32_t* sourc
   }
   ClusterLaunch cl;
   cl.cluster_size = heuristic_cluster_size(max_pitch);
-  {
-    TuneKey key{n_bucket(max_n), 0, ctx->num_sms};
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (auto& kv : g_tune)
-      if (kv.first == key) cl.cluster_size = kv.second.cluster_size;
-  }
+  if (have_tune && tv.engine == DJ_BATCH_ENGINE_CLUSTER) cl.cluster_size = tv.cluster_size;
   int rc = launch_cluster(reinterpret_cast<SolveDesc*>(ws), k, max_n, max_pitch,
                           reinterpret_cast<uint32_t*>(ws + tbytes), cl, st);
   cudaFreeAsync(ws, st);

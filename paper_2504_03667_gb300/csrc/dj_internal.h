@@ -32,6 +32,10 @@ struct dj_graph {
   // set by dj_graph_upload: the next solve waits for the kernels before it on its stream
   // before it reads the matrix (solves otherwise read the graph while the previous kernel ends)
   int32_t upload_pending = 0;
+  // lockstep batches: a column-tiled copy of the matrix for tiled_G slices (built on first use)
+  int32_t* tiled = nullptr;
+  int32_t tiled_G = 0;
+  uint64_t tiled_bytes = 0;
 };
 
 namespace dj {
@@ -162,6 +166,32 @@ struct ServeRing {
   int64_t idle_ns;
 };
 int run_serve_kernel(const ClusterPlan& plan, const ServeRing& r, cudaStream_t st);
+
+// A cooperative launch (every CTA resident at once), as a programmatic dependent of the previous
+// kernel on the stream when `pdl` (dj_solve.cu).
+cudaError_t launch_cooperative(void* fn, int G, int threads, void** args, size_t smem, cudaStream_t st, bool pdl);
+
+// Lockstep multi-source engine (dj_lockstep.cu): sources of one graph advance phase by phase
+// together over every SM; one source's outputs.
+struct LsSource {
+  int32_t* dist;
+  int32_t* pred;
+  int32_t source;
+  int32_t pad;
+};
+struct LockstepPlan {
+  int G = 0, TPS = 0, swmax = 0, S_max = 0, S = 0, groups = 0, k = 0, nvec_total = 0, rstride = 0;
+  size_t smem = 0, ws_bytes = 0, off_part = 0, off_dec = 0, off_tot = 0, off_reg = 0;
+};
+// Sizes and launch shape for k sources of g (groups of at most S_max sources, one launch each).
+int plan_lockstep(const dj_graph* g, int32_t k, LockstepPlan* plan);
+// The graph's column-tiled matrix copy for plan.G slices, built on `st` if missing.
+int lockstep_tiles(dj_graph* g, const LockstepPlan& plan, cudaStream_t st, const int32_t** out);
+// Launch every group.  ws: plan.ws_bytes of device memory whose first 256 bytes are zero (each
+// launch leaves them zero again); src_dev: the k sources' descriptors on the device.
+// allow_in = 0 keeps to the OUT bound (DJ_SETTLE_OUT).
+int run_lockstep(const dj_graph* g, const LockstepPlan& plan, const int32_t* tiled, const LsSource* src_dev,
+                 uint8_t* ws, uint32_t* words, int64_t timeout_ns, int allow_in, cudaStream_t st);
 int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters);
 bool cluster_config_ok(int32_t max_pitch, const ClusterLaunch& cl);
 

@@ -414,6 +414,7 @@ extern "C" int dj_graph_free(dj_graph* g) {
   cudaFree(g->row_ptr);
   cudaFree(g->col);
   cudaFree(g->wt);
+  cudaFree(g->tiled);
   delete g;
   return DJ_OK;
 }

@@ -35,6 +35,7 @@ DJ_ENGINE_AUTO, DJ_ENGINE_GRID, DJ_ENGINE_CLUSTER = 0, 1, 2
 DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN = 0, 1, 2
 DJ_FORMAT_DENSE, DJ_FORMAT_CSR = 0, 1
 DJ_COPIES_AUTO, DJ_COPIES_NARROW, DJ_COPIES_WIDE = 0, 1, 2
+DJ_BATCH_ENGINE_AUTO, DJ_BATCH_ENGINE_CLUSTER, DJ_BATCH_ENGINE_LOCKSTEP = 0, 1, 2
 
 
 class DjError(RuntimeError):
@@ -63,7 +64,7 @@ class dj_solve_opts(ctypes.Structure):
 class dj_batch_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("clusters", ctypes.c_int32), ("settle", ctypes.c_int32), ("copies", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class dj_serve_opts(ctypes.Structure):
@@ -116,6 +117,10 @@ SIGNATURES = {
     "dj_batch_free": (_INT, [_P]),
     "dj_batch_autotune": (_INT, [_P, _U64, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                  ctypes.POINTER(ctypes.c_float)]),
+    "dj_batch_get_engine": (_INT, [_P, ctypes.POINTER(_I32)]),
+    "dj_tune_load": (_INT, [ctypes.c_char_p]),
+    "dj_tune_save": (_INT, [ctypes.c_char_p]),
+    "dj_tune_lookup": (_INT, [_I32, _U64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "dj_serve_opts_init": (None, [ctypes.POINTER(dj_serve_opts)]),
     "dj_serve_create": (_INT, [ctypes.POINTER(dj_serve_opts), ctypes.POINTER(_P)]),
     "dj_serve_add_graph": (_INT, [_P, _P, ctypes.POINTER(_I32)]),
@@ -386,11 +391,13 @@ class Batch:
 
 
 def dj_batch_create(graphs: Sequence, sources, dists: Sequence, preds: Sequence, mode=DJ_MODE_AUTO,
-                    cluster_size=0, clusters=0, settle=DJ_SETTLE_AUTO, copies=0) -> Batch:
-    """copies: DJ_COPIES_AUTO (0), DJ_COPIES_NARROW (1) or DJ_COPIES_WIDE (2) ring copies."""
+                    cluster_size=0, clusters=0, settle=DJ_SETTLE_AUTO, copies=0, engine=DJ_BATCH_ENGINE_AUTO) -> Batch:
+    """copies: DJ_COPIES_AUTO (0), DJ_COPIES_NARROW (1) or DJ_COPIES_WIDE (2) ring copies.
+    engine: DJ_BATCH_ENGINE_AUTO (0), _CLUSTER (1) or _LOCKSTEP (2)."""
     o = dj_batch_opts()
     load_library().dj_batch_opts_init(ctypes.byref(o))
     o.mode, o.cluster_size, o.clusters, o.settle, o.copies = mode, cluster_size, clusters, settle, copies
+    o.engine = engine
     k = len(graphs)
     g = _ptr_array([_gh(x) for x in graphs])
     s = _host_i32(sources)
@@ -414,7 +421,31 @@ def dj_batch_autotune(b: Batch, stream=None) -> dict:
     c, t, ms = _I32(), _I32(), ctypes.c_float()
     _check(load_library().dj_batch_autotune(b.handle, _stream(stream), ctypes.byref(c), ctypes.byref(t),
                                             ctypes.byref(ms)))
-    return {"cluster_size": c.value, "threads": t.value, "ms": ms.value}
+    return {"cluster_size": c.value, "threads": t.value, "ms": ms.value, "engine": dj_batch_get_engine(b)}
+
+
+def dj_batch_get_engine(b: Batch) -> str:
+    e = _I32()
+    _check(load_library().dj_batch_get_engine(b.handle, ctypes.byref(e)))
+    return "lockstep" if e.value == DJ_BATCH_ENGINE_LOCKSTEP else "cluster"
+
+
+def dj_tune_load(path: str):
+    _check(load_library().dj_tune_load(os.fsencode(path)))
+
+
+def dj_tune_save(path: str):
+    _check(load_library().dj_tune_save(os.fsencode(path)))
+
+
+def dj_tune_lookup(n: int, entries: int, num_sms: int) -> Optional[dict]:
+    """The autotuner's entry for (n, finite entries, SM count), or None."""
+    e, c = _I32(), _I32()
+    rc = load_library().dj_tune_lookup(int(n), int(entries), int(num_sms), ctypes.byref(e), ctypes.byref(c))
+    if rc == DJ_EINVAL:
+        return None
+    _check(rc)
+    return {"engine": "lockstep" if e.value == DJ_BATCH_ENGINE_LOCKSTEP else "cluster", "cluster_size": c.value}
 
 
 # ---------------------------------------------------------------------- serving
