@@ -281,7 +281,7 @@ def main():
     per_launch_s = (ms_total / 1e3) / args.steps
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = _peaks()
-    traffic, traffic_note = _traffic(n)
+    traffic, traffic_note = _traffic(f"k_sssp_grid_dense_n{n}_traffic.txt", n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                 "frac_of_8tbs": achieved / 8000.0, "algorithmic_bytes_per_launch": alg_bytes,
@@ -324,9 +324,13 @@ def main():
         dist.destroy_process_group()
 
 
-def _traffic(n: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    path = os.path.join(ROOT, "profiles", f"k_sssp_grid_dense_n{n}_traffic.txt")
+TRAFFIC_FILES = {"dense_n1024_p0.1": "k_sssp_cluster_dense_n1024_traffic.txt",
+                 "sparse_directed_n32768_deg8": "k_sssp_grid_sparse_n32768_traffic.txt"}
+
+
+def _traffic(fname: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         kv = {}
         for ln in open(path):
@@ -336,8 +340,8 @@ def _traffic(n: int):
         if kv.get("kernel_source_hash") != _kernel_hash():
             return None, "kernel changed since the ncu capture"
         per = int(kv["dram_bytes_per_launch"])
-        return per, (f"ncu dram__bytes_read+write per launch at n={n} (1-pass capture, mean of 4 sources); "
-                     "below the algorithmic bytes because the column filter skips unchangeable slices")
+        return per, (f"ncu dram__bytes_read+write per launch at n={n} (1-pass capture, mean of the launches in "
+                     f"profiles/{fname})")
     except (OSError, KeyError, ValueError):
         return None, "no ncu capture"
 
@@ -535,6 +539,25 @@ def side_measurements(dj, torch, graphgen, g, e, srcs, stream) -> dict:
                     "phase_single_launch_value": single_rate, "vs_phase_single_launch": batch_rate / single_rate,
                     "cpu_baseline": batch_cpu_baseline(be, bs)}
     b.free()
+    # the same 256 solves on the lockstep multi-source engine (all sources advance phase by phase
+    # together, each row block read once per phase for every source that settles it)
+    lb = dj.dj_batch_create([bg] * k, bs, list(D), list(P), engine=dj.DJ_BATCH_ENGINE_LOCKSTEP)
+    for _ in range(2):
+        dj.dj_batch_launch(lb, stream)
+    dj.dj_sync(stream)
+    e0.record(stream)
+    for _ in range(reps):
+        dj.dj_batch_launch(lb, stream)
+    e1.record(stream)
+    e1.synchronize()
+    dj.dj_sync(stream)
+    lms = e0.elapsed_time(e1) / reps
+    out["batch_lockstep"] = {"workload": BATCH_WORKLOAD, "value": k / (lms / 1e3), "unit": "SSSP/s",
+                             "ms_per_batch": lms, "phases": dj.dj_last_phases(),
+                             "vs_cluster_engine": (k / (lms / 1e3)) / batch_rate,
+                             "what": "dj_batch_create(engine=DJ_BATCH_ENGINE_LOCKSTEP); not the default: slower "
+                                     "than the cluster engine here (bound by instruction issue)"}
+    lb.free()
     bg.free()
     out["serve"] = serving_measurement(dj, torch, graphgen, stream)
     return out
@@ -647,13 +670,14 @@ def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
     g.free()
     peak, peak_kind = _peaks()
     achieved = n * n * 4 / s_per / 1e9
+    traffic, traffic_note = _traffic(TRAFFIC_FILES[name], n) if name in TRAFFIC_FILES else (None, "no ncu capture")
     return {"value": 1.0 / s_per, "unit": "SSSP/s", "us_per_solve": 1e6 * s_per, "solves_timed": reps,
             "latency_us_alone": statistics.median(lat),
             "phases_first_source": phases if phases >= 0 else None,
             "engine": "grid" if (n >= 4096 or (n >= 2560 and info["entries"] * 4 >= n * n)) else "cluster",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "algorithmic_bytes_per_launch": n * n * 4,
-                         "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None},
+                         "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic, "traffic_note": traffic_note},
             "timer": "CUDA events over back-to-back dj_sssp calls (launch overhead included)"}
 
 
