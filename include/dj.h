@@ -187,9 +187,17 @@ typedef struct dj_solve_opts {
   int32_t reserved[2];
 } dj_solve_opts;
 
-#define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only */
+#define DJ_SETTLE_AUTO 0   /* OUT and IN bounds when every off-diagonal weight is >= 1, else OUT only;
+                              the IN bound dynamic where the graph keeps in-lists (below) */
 #define DJ_SETTLE_OUT 1    /* OUT bound only (nodes settled in Algorithm 1's visit order) */
-#define DJ_SETTLE_OUT_IN 2 /* OUT and IN bounds; falls back to OUT when some weight is 0 */
+#define DJ_SETTLE_OUT_IN 2 /* OUT and IN bounds, the IN bound from each column's smallest in-weight;
+                              falls back to OUT when some weight is 0 */
+#define DJ_SETTLE_OUT_DYN_IN 3 /* OUT and IN bounds, the IN bound (grid engine, graphs with fewer than
+                              n^2/32 finite entries, which keep each column's 4 smallest in-weights
+                              and their rows) from the smallest in-weight of the rows NOT yet settled:
+                              a shorter path into v must enter it from an unsettled row.  Fewer phases
+                              on sparse graphs (the directed n=32768, 8 out-edges per node graph:
+                              about 90 instead of 140); same results. */
 
 /* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */
 void dj_solve_opts_init(dj_solve_opts* opts);

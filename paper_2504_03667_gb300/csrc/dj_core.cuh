@@ -151,12 +151,20 @@ struct Slice {
   int32_t* pred;
   uint32_t* pdist;   // dist of pred[v] (the key's second field)
   uint32_t* minout;
-  uint32_t* minin;
+  uint32_t* minin;   // the IN bound's in-weight of each column (dynamic: from rows still unsettled)
   uint8_t* vis;
   int c0;    // first column (node id) of the slice, a multiple of 4
   int sw;    // columns in the slice, a multiple of 4
   int nvec;  // sw / 4
+  // dynamic IN bound (grid engine): the static minimum in-weight of each column (the tie
+  // sources belong to it), and the global word per node recording the phase it settled in
+  const uint32_t* minin0 = nullptr;
+  uint32_t* sph = nullptr;
+  uint32_t sph_stamp = 0;
 };
+
+// Whether column j's IN weight is still the static minimum (its tie sources apply).
+__device__ __forceinline__ bool minin_static(const Slice& s, int j) { return !s.minin0 || s.minin0[j] == s.minin[j]; }
 
 // Global decision of one phase.
 struct Decision {
@@ -546,7 +554,7 @@ __device__ __forceinline__ int live_groups(const Slice& s, const Decision& D, ui
       thr = t > thr ? t : thr;
       if (t == 0) continue;
       const uint32_t d = s.dist[col];
-      if (ties && t < (1ull << 32) && d < kInf && d == D.m + s.minin[col]) continue;
+      if (ties && t < (1ull << 32) && d < kInf && d == D.m + s.minin[col] && minin_static(s, col)) continue;
       if (rows && t == (1ull << 32)) {
         ++nimp;
         continue;
@@ -859,7 +867,7 @@ __device__ __forceinline__ int gather_column_pass(const Slice& s, const int32_t*
       const uint64_t t = column_live(s, col, D, bits_u);
       if (t == 0) continue;
       const uint32_t d = s.dist[col];
-      if (ts.cap > 0 && t < (1ull << 32) && D.use_in && d < kInf && d == D.m + s.minin[col]) {
+      if (ts.cap > 0 && t < (1ull << 32) && D.use_in && d < kInf && d == D.m + s.minin[col] && minin_static(s, col)) {
         tl[atomicAdd(&sc->cnt[28], 1u)] = static_cast<uint32_t>(col);
         continue;
       }
@@ -1278,7 +1286,10 @@ __device__ __forceinline__ void commit_column(const Slice& s, int col, uint64_t 
                                               uint32_t bits_u, Part& pt) {
   const uint32_t d = s.dist[col];
   const uint32_t tie0 = stored_tie(s, col, D, bits_u);
-  if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
+  if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) {
+    s.vis[col] = 1;
+    if (s.sph) s.sph[s.c0 + col] = s.sph_stamp;
+  }
   commit_key(s, col, b, tie0, D, bits_u);
   column_partial(s, col, pt);
 }
@@ -1362,6 +1373,36 @@ __device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, co
       b = x < b ? x : b;
     }
     one(col, b);
+  }
+}
+
+// Dynamic IN bound, after a commit: every unsettled node u has W[u][v] >= the smallest
+// in-weight of column v from rows still unsettled, so that weight may replace minin[v] in the IN
+// criterion and the column filter (a shorter path to v must enter it from an unsettled u, whose
+// dist is at least m).  Column v lists its kInLists smallest in-weights with their rows
+// (ascending) and a lower bound on the rest; cursor k0 skips listed rows known settled.  A row
+// counts as settled only once its phase stamp (phase + 1; 0 for the source) is at most `phase`,
+// i.e. it settled in an earlier phase: every CTA's commit of those phases precedes the barrier
+// this one passed, so the bound is the same in every run.  Rows settled since are treated as
+// unsettled, which only makes the bound smaller.  One row is checked per column and phase.
+struct DynIn {
+  const uint2* list;   // shared: [sw][kList] (weight, row)
+  const uint32_t* rest;
+  uint8_t* k0;
+  const uint32_t* sph;  // global phase stamps
+};
+template <int kList>
+__device__ __forceinline__ void dyn_in_update(const Slice& s, const DynIn& dy, uint32_t phase) {
+  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+    if (s.vis[j]) continue;
+    const int k = dy.k0[j];
+    if (k >= kList) continue;
+    const uint2 e = dy.list[j * kList + k];
+    if (e.x >= kInf) continue;  // no more in-edges listed: the bound is already INF
+    if (__ldcg(dy.sph + e.y) <= phase) {
+      dy.k0[j] = static_cast<uint8_t>(k + 1);
+      s.minin[j] = k + 1 < kList ? dy.list[j * kList + k + 1].x : dy.rest[j];
+    }
   }
 }
 

@@ -22,6 +22,11 @@ struct dj_graph {
   int32_t* tsrc = nullptr;    // n x tcap tie sources: the u != v with W[u][v] == minin[v]
   int32_t* tcnt = nullptr;    // n counts (above tcap: not listed)
   int32_t tcap = 0;
+  // graphs that are not dense: the kInLists smallest finite in-weights of every column with their
+  // rows, ascending by (weight, row), and a lower bound on every other in-weight (the dynamic IN
+  // bound of the grid engine); nullptr otherwise
+  uint2* inlist = nullptr;     // n x kInLists (weight, row); (INF, ~0) where a column has fewer
+  uint32_t* inrest = nullptr;  // n: the kInLists-th weight if the column has more in-edges, else INF
   uint64_t bytes = 0;
   uint64_t entries = 0;       // finite off-diagonal matrix entries (directed edges)
   int32_t format = DJ_FORMAT_DENSE;  // DJ_FORMAT_CSR: no matrix, the arrays below
@@ -39,6 +44,8 @@ struct dj_graph {
 };
 
 namespace dj {
+
+constexpr int kInLists = 4;  // in-edges listed per column for the dynamic IN bound
 
 // Descriptor of one solve for the cluster engine (64 bytes).
 struct SolveDesc {

@@ -135,6 +135,45 @@ __global__ void k_tiesrc(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   }
 }
 
+// In-lists: for every column v the kInLists smallest finite off-diagonal weights W[u][v] with
+// their rows u, ascending by (weight, row), and a lower bound on every other in-weight (the
+// kInLists-th weight when the column has more in-edges, INF otherwise).  One thread per column
+// reads its column top to bottom (a warp reads 128 contiguous bytes per row).
+__global__ void k_inlist(const int32_t* __restrict__ W, int64_t pitch, int32_t n, uint2* __restrict__ inlist,
+                         uint32_t* __restrict__ inrest) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint64_t k[kInLists];
+#pragma unroll
+  for (int i = 0; i < kInLists; ++i) k[i] = ~0ull;
+  uint32_t cnt = 0;
+  const int32_t* col = W + v;
+  for (int64_t u0 = 0; u0 < n; u0 += 8) {
+    uint32_t w8[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) w8[r] = u0 + r < n ? static_cast<uint32_t>(__ldg(col + (u0 + r) * pitch)) : kInf;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t u = u0 + r;
+      if (w8[r] >= kInf || u == v) continue;
+      ++cnt;
+      uint64_t key = (static_cast<uint64_t>(w8[r]) << 32) | static_cast<uint32_t>(u);
+#pragma unroll
+      for (int i = 0; i < kInLists; ++i)  // insertion into the sorted list
+        if (key < k[i]) {
+          const uint64_t t = k[i];
+          k[i] = key;
+          key = t;
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kInLists; ++i)
+    inlist[v * kInLists + i] = k[i] == ~0ull ? make_uint2(kInf, 0xFFFFFFFFu)
+                                             : make_uint2(static_cast<uint32_t>(k[i] >> 32), static_cast<uint32_t>(k[i]));
+  inrest[v] = cnt > static_cast<uint32_t>(kInLists) ? static_cast<uint32_t>(k[kInLists - 1] >> 32) : kInf;
+}
+
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t value) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -205,8 +244,12 @@ static int alloc_graph(int32_t n, int directed, dj_graph** out) {
   return DJ_OK;
 }
 
+static void launch_inlists(dj_graph* g, cudaStream_t st) {
+  k_inlist<<<static_cast<unsigned>((g->n + 127) / 128), 128, 0, st>>>(g->W, g->pitch, g->n, g->inlist, g->inrest);
+}
+
 // Column minima (a copy of the row minima for undirected graphs, else
-// k_colmin), then the columns' tie sources.
+// k_colmin), then the columns' tie sources (and in-lists, where the graph keeps them).
 static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
   k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
   if (!g->directed) {
@@ -219,6 +262,7 @@ static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
   cudaMemsetAsync(g->tcnt, 0, static_cast<size_t>(g->n) * sizeof(int32_t), st);
   dim3 tgrid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
   k_tiesrc<<<tgrid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc, g->tcnt, g->tcap);
+  if (g->inlist) launch_inlists(g, st);
 }
 
 // Row and column minima + global weight range, then the overflow rule (n-1) * wmax < INT32_MAX.
@@ -239,6 +283,22 @@ static int finish_graph(dj_graph* g, cudaStream_t st) {
   g->entries = static_cast<uint64_t>(res[2]) | (static_cast<uint64_t>(res[3]) << 32);
   if (g->n > 1 && static_cast<int64_t>(g->n - 1) * g->wmax >= static_cast<int64_t>(DJ_INF))
     return set_error(DJ_EOVERFLOW, "(n-1) * max weight >= INT32_MAX: path lengths could overflow int32");
+  // graphs that are not dense keep in-lists for the grid engine's dynamic IN bound
+  const uint64_t nn = static_cast<uint64_t>(g->n) * static_cast<uint64_t>(g->n);
+  if (g->entries * 32 < nn && g->wmin >= 1 && !g->inlist) {
+    const size_t lb = static_cast<size_t>(g->n) * kInLists * sizeof(uint2), rb = static_cast<size_t>(g->n) * 4;
+    uint8_t* buf = nullptr;
+    if (cudaMalloc(&buf, lb + rb) == cudaSuccess) {
+      g->inlist = reinterpret_cast<uint2*>(buf);
+      g->inrest = reinterpret_cast<uint32_t*>(buf + lb);
+      g->bytes += lb + rb;
+      launch_inlists(g, st);
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_error(e, "building the in-lists");
+    } else {
+      cudaGetLastError();  // no room: the static IN bound only
+    }
+  }
   return DJ_OK;
 }
 
@@ -411,6 +471,7 @@ extern "C" int dj_graph_free(dj_graph* g) {
   cudaFree(g->W);
   cudaFree(g->minout);  // minin shares this allocation
   cudaFree(g->tsrc);    // tcnt shares this allocation
+  cudaFree(g->inlist);  // inrest shares this allocation
   cudaFree(g->row_ptr);
   cudaFree(g->col);
   cudaFree(g->wt);

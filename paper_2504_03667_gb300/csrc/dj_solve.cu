@@ -67,6 +67,11 @@ struct GridParams {
   unsigned long long* gkey;  // [2][pitch] merged row-split keys per phase parity, all ones between uses
   TieSources ts;       // the columns' tie sources (cap 0: not used)
   int32_t sym;         // the matrix is symmetric (undirected graph): column v is row v
+  // dynamic IN bound (dyn_in != 0): the columns' in-lists and the per-node settle-phase stamps
+  const uint2* inlist;
+  const uint32_t* inrest;
+  uint32_t* sph;
+  int32_t dyn_in;
 };
 
 constexpr int kMaxPartialsPerLane = 10;  // the decision warp reads up to 320 CTA partials
@@ -139,6 +144,33 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
   q += (static_cast<size_t>(p.swcap) / 4 + 3) / 4 * 16;
   uint32_t* list = reinterpret_cast<uint32_t*>(q);  // staged settled rows
   q += static_cast<size_t>(p.list_cap) * 4;
+  DynIn dy{nullptr, nullptr, nullptr, p.sph};
+  if (p.dyn_in) {  // in-lists of the slice's columns, their rest bounds, cursors and static minima
+    uint2* il = reinterpret_cast<uint2*>(q);
+    q += static_cast<size_t>(p.swcap) * kInLists * 8;
+    uint32_t* ir = reinterpret_cast<uint32_t*>(q);
+    q += static_cast<size_t>(p.swcap) * 4;
+    uint32_t* m0 = reinterpret_cast<uint32_t*>(q);
+    q += static_cast<size_t>(p.swcap) * 4;
+    uint8_t* k0 = q;
+    q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+    for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+      const int v = s.c0 + j;
+      const bool real = v < p.n;
+#pragma unroll
+      for (int i = 0; i < kInLists; ++i)
+        il[j * kInLists + i] = real ? __ldg(p.inlist + static_cast<size_t>(v) * kInLists + i) : make_uint2(kInf, ~0u);
+      ir[j] = real ? __ldg(p.inrest + v) : kInf;
+      m0[j] = real ? static_cast<uint32_t>(__ldg(p.minout + p.n + v)) : kInf;
+      k0[j] = 0;
+      if (real) p.sph[v] = v == p.source ? 0u : 0xFFFFFFFFu;  // ordered before use by the first barrier
+    }
+    dy.list = il;
+    dy.rest = ir;
+    dy.k0 = k0;
+    s.minin0 = m0;
+    s.sph = p.sph;
+  }
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* rings = q;  // the warps' TMA rings; in row-split phases the two row buffers
@@ -190,6 +222,7 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? p.trace + 8 * phase
                                                                                            : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = global_ns();
+    s.sph_stamp = phase + 1;  // the stamp this phase's commits write (the source's is 0)
     // 1. publish this slice's partial and its candidates (into its own region)
     uint4* out = p.cand + (static_cast<size_t>(phase & 1) * G + b) * p.swcap;
     uint64_t key;
@@ -377,6 +410,10 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
       if (tr && threadIdx.x == 0) tr[5] = global_ns();
       // 5. merge, mark, commit, and the next partial
       commit_partial<V>(s, t, D, merge, p.bits_u, best, part);
+    }
+    if (p.dyn_in) {  // the next phase's IN weights: rows settled in earlier phases drop out
+      __syncthreads();
+      dyn_in_update<kInLists>(s, dy, phase);
     }
     if (tr && threadIdx.x == 0) tr[6] = global_ns();
     ++phase;
@@ -744,6 +781,7 @@ struct Layout {
   int srows = 0;    // rows per stage (<= kRowsPerStage)
   int list_cap = 0; // staged settled rows per segment
   bool filter = false;  // grid engine: per-column keys and live groups of the filtered relaxation
+  bool dyn = false;     // grid engine: in-lists, rest bounds, static minima and cursors (dynamic IN)
   bool amerge = false;  // row groups merge by atomicMin into one key per column (no merge rows)
   size_t rs_bytes = 0;  // grid engine: the two row-split buffers (share the ring region)
   int rowcap = 0;   // bytes of one ring row slot
@@ -764,6 +802,8 @@ size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
   b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
   b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
   b += static_cast<size_t>(L.list_cap) * 4;                                      // staged rows
+  if (L.dyn)
+    b += static_cast<size_t>(L.swcap) * (kInLists * 8 + 8) + (static_cast<size_t>(L.swcap) + 15) / 16 * 16;
   if (L.filter)  // per-column keys, group thresholds, live groups
     b += static_cast<size_t>(L.swcap) * 8 + static_cast<size_t>(L.swcap) / 4 * 8 +
          (static_cast<size_t>(L.swcap) / 4 + 3) / 4 * 16;
@@ -885,6 +925,10 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   L.list_cap = std::min(nvec_total * 4, kGridListCap);
   // row split pays on dense graphs (few phases, thousands of rows each); auto: density >= 1/32
   const bool dense = g->entries * 32 >= static_cast<uint64_t>(g->n) * static_cast<uint64_t>(g->n);
+  // the dynamic IN bound (graphs that keep in-lists: not dense, every weight >= 1)
+  const bool dyn_in = o.mode != DJ_MODE_PLAIN && g->inlist && g->wmin >= 1 &&
+                      (o.settle == DJ_SETTLE_AUTO || o.settle == DJ_SETTLE_OUT_DYN_IN);
+  L.dyn = dyn_in;
   const bool want_rs = o.mode != DJ_MODE_PLAIN && (o.rowsplit > 0 || (o.rowsplit == 0 && dense));
   L.rs_bytes = want_rs ? static_cast<size_t>(2) * std::min(nvec_total, kGridThreads * kRowSplitCpt) * 16 : 0;
   if (make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L) != DJ_OK) {
@@ -920,9 +964,10 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                                                                                            : 0;
   const size_t snap_bytes = rs_min > 0 ? static_cast<size_t>(g->pitch) * 4 : 0;  // pitch is a multiple of 4
   const size_t gkey_bytes = (rs_min > 0 || rp_min > 0) ? static_cast<size_t>(2) * g->pitch * 8 : 0;
+  const size_t sph_bytes = dyn_in ? static_cast<size_t>(g->pitch) * 4 : 0;
   // the stream's kept workspace (its control words are zero between launches: see grid_exit),
   // or one allocated for this call
-  const size_t ws_bytes = ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes;
+  const size_t ws_bytes = ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes + sph_bytes;
   uint8_t* ws = nullptr;
   if (int rc = stream_workspace(ctx, st, ws_bytes, ctl_bytes, &ws)) return rc;
   const bool own_ws = ws == nullptr;
@@ -973,6 +1018,11 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                : nullptr;
   p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
+  p.dyn_in = dyn_in && p.use_in ? 1 : 0;
+  p.inlist = g->inlist;
+  p.inrest = g->inrest;
+  p.sph = dyn_in ? reinterpret_cast<uint32_t*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes)
+                 : nullptr;
   void* args[] = {&p};
   e = launch_cooperative(fn, G, kGridThreads, args, L.smem, st, true);
   if (own_ws) cudaFreeAsync(ws, st);
@@ -1328,6 +1378,10 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.gkey = nullptr;
   p.ts = p.use_in && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
+  p.dyn_in = 0;  // no room for the phase stamps in the fixed scratch
+  p.inlist = nullptr;
+  p.inrest = nullptr;
+  p.sph = nullptr;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(grid engine)");

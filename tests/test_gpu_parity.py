@@ -30,13 +30,14 @@ def dj():
     return _dj
 
 
-def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0, rowsplit=0, rowpush=0):
+def solve(dj, g, s, engine=0, mode=0, cluster_size=0, live=0, rowsplit=0, rowpush=0, settle=0):
     import torch
     n = dj.dj_graph_get_info(g)["n"]
     dist = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     pred = torch.full((n,), -5, dtype=torch.int32, device="cuda")
     dj.dj_sssp_ex(g, s, dist, pred, dj.make_solve_opts(mode=mode, engine=engine, cluster_size=cluster_size,
-                                                       live=live, rowsplit=rowsplit, rowpush=rowpush))
+                                                       live=live, rowsplit=rowsplit, rowpush=rowpush,
+                                                       settle=settle))
     dj.dj_sync()
     return dist.cpu().numpy(), pred.cpu().numpy()
 
@@ -217,6 +218,10 @@ def test_sparse_directed_n32768_full(dj, orc):
     W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
     ref = orc.dijkstra(W, s)
     assert_same(solve(dj, G, s), ref, "n=32768 directed")  # the launch the benchmark times
+    dyn_phases = dj.dj_last_phases()
+    assert_same(solve(dj, G, s, engine=1, settle=2), ref, "n=32768 directed, static IN bound")
+    static_phases = dj.dj_last_phases()
+    assert dyn_phases < static_phases  # the dynamic IN bound settles more per phase
     assert_same(solve(dj, G, s, engine=1, rowpush=-1), ref, "n=32768 directed, row push off")
     assert_same(solve(dj, G, s, engine=1, rowpush=1), ref, "n=32768 directed, row push in every phase")
     assert_same(solve(dj, G, s, engine=2, cluster_size=16), ref, "n=32768 directed, cluster engine")
@@ -413,3 +418,33 @@ def test_back_to_back_grid_solves_and_upload(dj, orc):
     assert_same((d2.cpu().numpy(), p2.cpu().numpy()), orc.dijkstra(W3, 3), "after upload")
     G.free()
     G2.free()
+
+
+def test_dynamic_in_bound(dj, orc):
+    """On graphs that are not dense the grid engine takes the IN bound from the smallest in-weight
+    of the rows still unsettled (each column's four smallest in-weights listed at load).  Static,
+    dynamic and OUT-only settle bounds, on ragged tie-heavy directed and undirected graphs, columns
+    with more in-edges than listed and fewer, all give Algorithm 1's dist and pred; the dynamic
+    bound never takes more phases than the static one."""
+    cases = [
+        ("directed ties", graphgen.random_edges(5003, 6 * 5003, 1, 3, seed=101, directed=True)),
+        ("undirected ties", graphgen.random_edges(4099, 5 * 4099, 1, 4, seed=102, directed=False)),
+        ("directed wide weights", graphgen.outdeg(6000, 8, 1, 10000, seed=103)),
+        ("in-degree about 40", graphgen.random_edges(4000, 40 * 4000, 1, 20, seed=104, directed=True)),
+        ("few in-edges", graphgen.random_edges(3001, 2 * 3001, 1, 9, seed=105, directed=True)),
+    ]
+    for what, e in cases:
+        G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, e.directed)
+        W = orc.build_matrix(e.n, e.src, e.dst, e.w, e.directed)
+        for s in (0, e.n // 2, e.n - 1):
+            ref = orc.dijkstra(W, s)
+            assert_same(solve(dj, G, s, engine=1, settle=3), ref, f"{what} s={s} dynamic IN")
+            ph_dyn = dj.dj_last_phases()
+            assert_same(solve(dj, G, s, engine=1, settle=2), ref, f"{what} s={s} static IN")
+            ph_static = dj.dj_last_phases()
+            assert_same(solve(dj, G, s, engine=1, settle=1), ref, f"{what} s={s} OUT only")
+            assert_same(solve(dj, G, s, engine=1, settle=3, rowpush=1), ref, f"{what} s={s} dynamic IN, row push")
+            assert_same(solve(dj, G, s, engine=1, settle=3, live=1 << 20, rowpush=-1), ref,
+                        f"{what} s={s} dynamic IN, gather")
+            assert ph_dyn <= ph_static, (what, s, ph_dyn, ph_static)
+        G.free()
