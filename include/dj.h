@@ -198,6 +198,11 @@ typedef struct dj_solve_opts {
                               a shorter path into v must enter it from an unsettled row.  Fewer phases
                               on sparse graphs (the directed n=32768, 8 out-edges per node graph:
                               about 90 instead of 140); same results. */
+#define DJ_SETTLE_DYN 4    /* DJ_SETTLE_OUT_DYN_IN and the OUT bound dynamic too: each row's smallest
+                              out-weight to columns not yet settled (rows' 4 smallest out-weights listed
+                              at load).  A few phases fewer again (85 instead of 89 on that graph), but
+                              the lists take shared memory from the streaming rings (measured slower
+                              there: 1822 against 1739 us), so not the default. */
 
 /* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */
 void dj_solve_opts_init(dj_solve_opts* opts);

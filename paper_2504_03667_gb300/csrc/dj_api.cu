@@ -179,7 +179,7 @@ extern "C" int dj_sssp_ex(const dj_graph* g, int32_t source, int32_t* dist, int3
   dj_solve_opts_init(&o);
   if (opts) o = *opts;
   if (o.mode < DJ_MODE_AUTO || o.mode > DJ_MODE_PLAIN) return set_error(DJ_EINVAL, "unknown mode");
-  if (o.settle < DJ_SETTLE_AUTO || o.settle > DJ_SETTLE_OUT_DYN_IN) return set_error(DJ_EINVAL, "unknown settle bounds");
+  if (o.settle < DJ_SETTLE_AUTO || o.settle > DJ_SETTLE_DYN) return set_error(DJ_EINVAL, "unknown settle bounds");
   if (o.live < -1) return set_error(DJ_EINVAL, "live must be -1, 0 or a group count");
   if (o.rowsplit < -1) return set_error(DJ_EINVAL, "rowsplit must be -1, 0 or a candidate count");
   if (o.rowpush < -1) return set_error(DJ_EINVAL, "rowpush must be -1, 0 or a candidate count");

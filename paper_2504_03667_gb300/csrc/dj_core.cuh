@@ -1385,23 +1385,43 @@ __device__ __forceinline__ void commit_partial(const Slice& s, const Tile& t, co
 // i.e. it settled in an earlier phase: every CTA's commit of those phases precedes the barrier
 // this one passed, so the bound is the same in every run.  Rows settled since are treated as
 // unsettled, which only makes the bound smaller.  One row is checked per column and phase.
+// The same for the OUT bound (dynamic OUT): every unsettled u and unsettled w != u have
+// W[u][w] >= the smallest out-weight of row u to columns still unsettled, which may replace
+// minout[u] in L = min over unsettled u of dist[u] + minout[u].  If an unsettled x with dist[x] < L
+// were not final, take on a shortest path to x the first unsettled node y whose successor z is
+// unsettled (one exists: otherwise x's predecessor is settled and dist[x] is exact); y's
+// predecessor is settled, so dist[y] is exact and the path is at least dist[y] + W[y][z] >= L.
+// L also still bounds every offer that could change a settled column v (the column filter's use
+// of it): only a tie can, from a row u unsettled now; a column settled in the previous phase is
+// not yet excluded from u's minimum, and one settled earlier cannot be tied by such a u at all
+// (had v been settled by the IN bound, u would have been at dist m then and settled with it; by
+// the OUT bound, every u with dist[u] < dist[v] was final then and settled with it).
 struct DynIn {
-  const uint2* list;   // shared: [sw][kList] (weight, row)
+  const uint2* list;   // shared: [sw][kList] (weight, row) of the columns' in-edges
   const uint32_t* rest;
   uint8_t* k0;
+  const uint2* olist;  // shared: [sw][kList] (weight, column) of the slice's nodes' out-edges
+  const uint32_t* orest;
+  uint8_t* ok0;
   const uint32_t* sph;  // global phase stamps
 };
 template <int kList>
 __device__ __forceinline__ void dyn_in_update(const Slice& s, const DynIn& dy, uint32_t phase) {
   for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
     if (s.vis[j]) continue;
-    const int k = dy.k0[j];
-    if (k >= kList) continue;
-    const uint2 e = dy.list[j * kList + k];
-    if (e.x >= kInf) continue;  // no more in-edges listed: the bound is already INF
-    if (__ldcg(dy.sph + e.y) <= phase) {
+    const int k = dy.k0[j], ko = dy.olist ? dy.ok0[j] : kList;
+    const uint2 e = k < kList ? dy.list[j * kList + k] : make_uint2(kInf, 0u);
+    const uint2 eo = ko < kList ? dy.olist[j * kList + ko] : make_uint2(kInf, 0u);
+    // both checks' loads in flight together; an exhausted list (INF entry) keeps its bound
+    const uint32_t sp = e.x < kInf ? __ldcg(dy.sph + e.y) : 0xFFFFFFFFu;
+    const uint32_t spo = eo.x < kInf ? __ldcg(dy.sph + eo.y) : 0xFFFFFFFFu;
+    if (sp <= phase) {
       dy.k0[j] = static_cast<uint8_t>(k + 1);
       s.minin[j] = k + 1 < kList ? dy.list[j * kList + k + 1].x : dy.rest[j];
+    }
+    if (spo <= phase) {
+      dy.ok0[j] = static_cast<uint8_t>(ko + 1);
+      s.minout[j] = ko + 1 < kList ? dy.olist[j * kList + ko + 1].x : dy.orest[j];
     }
   }
 }

@@ -27,6 +27,10 @@ struct dj_graph {
   // bound of the grid engine); nullptr otherwise
   uint2* inlist = nullptr;     // n x kInLists (weight, row); (INF, ~0) where a column has fewer
   uint32_t* inrest = nullptr;  // n: the kInLists-th weight if the column has more in-edges, else INF
+  // the same for rows (out-edges, for the dynamic OUT bound): the in-lists themselves when the
+  // matrix is symmetric (undirected graph)
+  uint2* outlist = nullptr;
+  uint32_t* outrest = nullptr;
   uint64_t bytes = 0;
   uint64_t entries = 0;       // finite off-diagonal matrix entries (directed edges)
   int32_t format = DJ_FORMAT_DENSE;  // DJ_FORMAT_CSR: no matrix, the arrays below

@@ -174,6 +174,57 @@ __global__ void k_inlist(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   inrest[v] = cnt > static_cast<uint32_t>(kInLists) ? static_cast<uint32_t>(k[kInLists - 1] >> 32) : kInf;
 }
 
+// Out-lists: for every row u the kInLists smallest finite off-diagonal weights W[u][v] with their
+// columns, ascending by (weight, column), and the lower bound on the others (as k_inlist).  One
+// warp per row: each lane keeps the smallest of its columns, then the warp takes the list's
+// entries one by one as the minimum of the lanes' heads.
+__global__ void k_outlist(const int32_t* __restrict__ W, int64_t pitch, int32_t n, uint2* __restrict__ outlist,
+                          uint32_t* __restrict__ outrest) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t* row = W + u * pitch;
+    uint64_t k[kInLists];
+#pragma unroll
+    for (int i = 0; i < kInLists; ++i) k[i] = ~0ull;
+    uint32_t cnt = 0;
+    for (int64_t v = lane; v < n; v += 32) {
+      const uint32_t w = static_cast<uint32_t>(__ldg(row + v));
+      if (w >= kInf || v == u) continue;
+      ++cnt;
+      uint64_t key = (static_cast<uint64_t>(w) << 32) | static_cast<uint32_t>(v);
+#pragma unroll
+      for (int i = 0; i < kInLists; ++i)
+        if (key < k[i]) {
+          const uint64_t t = k[i];
+          k[i] = key;
+          key = t;
+        }
+    }
+    cnt = warp_sum_u32(cnt);
+    uint64_t out[kInLists];
+#pragma unroll
+    for (int i = 0; i < kInLists; ++i) {  // the warp's i-th smallest: the minimum of the lanes' heads
+      const uint64_t mn = warp_min_u64(k[0]);
+      out[i] = mn;
+      if (k[0] == mn && mn != ~0ull) {  // keys are distinct (the column is in the key): one lane pops
+#pragma unroll
+        for (int j = 0; j + 1 < kInLists; ++j) k[j] = k[j + 1];
+        k[kInLists - 1] = ~0ull;
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < kInLists; ++i)
+        outlist[u * kInLists + i] = out[i] == ~0ull ? make_uint2(kInf, 0xFFFFFFFFu)
+                                                    : make_uint2(static_cast<uint32_t>(out[i] >> 32),
+                                                                 static_cast<uint32_t>(out[i]));
+      outrest[u] = cnt > static_cast<uint32_t>(kInLists) ? static_cast<uint32_t>(out[kInLists - 1] >> 32) : kInf;
+    }
+  }
+}
+
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t value) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -246,6 +297,8 @@ static int alloc_graph(int32_t n, int directed, dj_graph** out) {
 
 static void launch_inlists(dj_graph* g, cudaStream_t st) {
   k_inlist<<<static_cast<unsigned>((g->n + 127) / 128), 128, 0, st>>>(g->W, g->pitch, g->n, g->inlist, g->inrest);
+  if (g->outlist != g->inlist)
+    k_outlist<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->outlist, g->outrest);
 }
 
 // Column minima (a copy of the row minima for undirected graphs, else
@@ -287,11 +340,15 @@ static int finish_graph(dj_graph* g, cudaStream_t st) {
   const uint64_t nn = static_cast<uint64_t>(g->n) * static_cast<uint64_t>(g->n);
   if (g->entries * 32 < nn && g->wmin >= 1 && !g->inlist) {
     const size_t lb = static_cast<size_t>(g->n) * kInLists * sizeof(uint2), rb = static_cast<size_t>(g->n) * 4;
+    const int lists = g->directed ? 2 : 1;  // a symmetric matrix's out-lists are its in-lists
     uint8_t* buf = nullptr;
-    if (cudaMalloc(&buf, lb + rb) == cudaSuccess) {
+    // [in-lists][out-lists][in rests][out rests]: the 8-byte entries first, at multiples of 32 n bytes
+    if (cudaMalloc(&buf, lists * (lb + rb)) == cudaSuccess) {
       g->inlist = reinterpret_cast<uint2*>(buf);
-      g->inrest = reinterpret_cast<uint32_t*>(buf + lb);
-      g->bytes += lb + rb;
+      g->outlist = lists == 2 ? reinterpret_cast<uint2*>(buf + lb) : g->inlist;
+      g->inrest = reinterpret_cast<uint32_t*>(buf + lists * lb);
+      g->outrest = lists == 2 ? reinterpret_cast<uint32_t*>(buf + 2 * lb + rb) : g->inrest;
+      g->bytes += lists * (lb + rb);
       launch_inlists(g, st);
       e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_error(e, "building the in-lists");

@@ -70,6 +70,8 @@ struct GridParams {
   // dynamic IN bound (dyn_in != 0): the columns' in-lists and the per-node settle-phase stamps
   const uint2* inlist;
   const uint32_t* inrest;
+  const uint2* outlist;
+  const uint32_t* outrest;
   uint32_t* sph;
   int32_t dyn_in;
 };
@@ -144,23 +146,37 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
   q += (static_cast<size_t>(p.swcap) / 4 + 3) / 4 * 16;
   uint32_t* list = reinterpret_cast<uint32_t*>(q);  // staged settled rows
   q += static_cast<size_t>(p.list_cap) * 4;
-  DynIn dy{nullptr, nullptr, nullptr, p.sph};
-  if (p.dyn_in) {  // in-lists of the slice's columns, their rest bounds, cursors and static minima
+  DynIn dy{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, p.sph};
+  if (p.dyn_in) {  // in- (and out-) lists of the slice's nodes, rest bounds, cursors, static minima
+    const bool dout = (p.dyn_in & 2) != 0;
     uint2* il = reinterpret_cast<uint2*>(q);
     q += static_cast<size_t>(p.swcap) * kInLists * 8;
+    uint2* ol = reinterpret_cast<uint2*>(q);
+    if (dout) q += static_cast<size_t>(p.swcap) * kInLists * 8;
     uint32_t* ir = reinterpret_cast<uint32_t*>(q);
     q += static_cast<size_t>(p.swcap) * 4;
+    uint32_t* orr = reinterpret_cast<uint32_t*>(q);
+    if (dout) q += static_cast<size_t>(p.swcap) * 4;
     uint32_t* m0 = reinterpret_cast<uint32_t*>(q);
     q += static_cast<size_t>(p.swcap) * 4;
     uint8_t* k0 = q;
     q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+    uint8_t* ok0 = q;
+    if (dout) q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
     for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
       const int v = s.c0 + j;
       const bool real = v < p.n;
 #pragma unroll
-      for (int i = 0; i < kInLists; ++i)
+      for (int i = 0; i < kInLists; ++i) {
         il[j * kInLists + i] = real ? __ldg(p.inlist + static_cast<size_t>(v) * kInLists + i) : make_uint2(kInf, ~0u);
+        if (dout)
+          ol[j * kInLists + i] = real ? __ldg(p.outlist + static_cast<size_t>(v) * kInLists + i) : make_uint2(kInf, ~0u);
+      }
       ir[j] = real ? __ldg(p.inrest + v) : kInf;
+      if (dout) {
+        orr[j] = real ? __ldg(p.outrest + v) : kInf;
+        ok0[j] = 0;
+      }
       m0[j] = real ? static_cast<uint32_t>(__ldg(p.minout + p.n + v)) : kInf;
       k0[j] = 0;
       if (real) p.sph[v] = v == p.source ? 0u : 0xFFFFFFFFu;  // ordered before use by the first barrier
@@ -168,6 +184,11 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     dy.list = il;
     dy.rest = ir;
     dy.k0 = k0;
+    if (dout) {
+      dy.olist = ol;
+      dy.orest = orr;
+      dy.ok0 = ok0;
+    }
     s.minin0 = m0;
     s.sph = p.sph;
   }
@@ -781,7 +802,7 @@ struct Layout {
   int srows = 0;    // rows per stage (<= kRowsPerStage)
   int list_cap = 0; // staged settled rows per segment
   bool filter = false;  // grid engine: per-column keys and live groups of the filtered relaxation
-  bool dyn = false;     // grid engine: in-lists, rest bounds, static minima and cursors (dynamic IN)
+  int dyn = 0;          // grid engine: 1 in-lists (dynamic IN), 2 also out-lists (dynamic OUT), with rests and cursors
   bool amerge = false;  // row groups merge by atomicMin into one key per column (no merge rows)
   size_t rs_bytes = 0;  // grid engine: the two row-split buffers (share the ring region)
   int rowcap = 0;   // bytes of one ring row slot
@@ -802,8 +823,10 @@ size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
   b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
   b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
   b += static_cast<size_t>(L.list_cap) * 4;                                      // staged rows
-  if (L.dyn)
-    b += static_cast<size_t>(L.swcap) * (kInLists * 8 + 8) + (static_cast<size_t>(L.swcap) + 15) / 16 * 16;
+  if (L.dyn)  // lists, rests and cursors (one or two sets) and the static minima
+    b += static_cast<size_t>(L.dyn) * (static_cast<size_t>(L.swcap) * (kInLists * 8 + 4) +
+                                       (static_cast<size_t>(L.swcap) + 15) / 16 * 16) +
+         static_cast<size_t>(L.swcap) * 4;
   if (L.filter)  // per-column keys, group thresholds, live groups
     b += static_cast<size_t>(L.swcap) * 8 + static_cast<size_t>(L.swcap) / 4 * 8 +
          (static_cast<size_t>(L.swcap) / 4 + 3) / 4 * 16;
@@ -925,10 +948,15 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   L.list_cap = std::min(nvec_total * 4, kGridListCap);
   // row split pays on dense graphs (few phases, thousands of rows each); auto: density >= 1/32
   const bool dense = g->entries * 32 >= static_cast<uint64_t>(g->n) * static_cast<uint64_t>(g->n);
-  // the dynamic IN bound (graphs that keep in-lists: not dense, every weight >= 1)
-  const bool dyn_in = o.mode != DJ_MODE_PLAIN && g->inlist && g->wmin >= 1 &&
-                      (o.settle == DJ_SETTLE_AUTO || o.settle == DJ_SETTLE_OUT_DYN_IN);
-  L.dyn = dyn_in;
+  // the dynamic IN bound, and with DJ_SETTLE_DYN also the dynamic OUT bound (graphs that keep
+  // in-lists: not dense, every weight >= 1)
+  const bool dyn_ok = o.mode != DJ_MODE_PLAIN && g->inlist && g->wmin >= 1;
+  const int dyn = !dyn_ok ? 0
+                  : (o.settle == DJ_SETTLE_AUTO || o.settle == DJ_SETTLE_OUT_DYN_IN) ? 1
+                  : o.settle == DJ_SETTLE_DYN                                         ? 2
+                                                                                      : 0;
+  const bool dyn_in = dyn > 0;
+  L.dyn = dyn;
   const bool want_rs = o.mode != DJ_MODE_PLAIN && (o.rowsplit > 0 || (o.rowsplit == 0 && dense));
   L.rs_bytes = want_rs ? static_cast<size_t>(2) * std::min(nvec_total, kGridThreads * kRowSplitCpt) * 16 : 0;
   if (make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L) != DJ_OK) {
@@ -1018,9 +1046,11 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
                : nullptr;
   p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
-  p.dyn_in = dyn_in && p.use_in ? 1 : 0;
+  p.dyn_in = dyn_in && p.use_in ? (dyn == 2 ? 3 : 1) : 0;  // bit 0: IN lists, bit 1: OUT lists
   p.inlist = g->inlist;
   p.inrest = g->inrest;
+  p.outlist = g->outlist;
+  p.outrest = g->outrest;
   p.sph = dyn_in ? reinterpret_cast<uint32_t*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes + gkey_bytes)
                  : nullptr;
   void* args[] = {&p};
@@ -1381,6 +1411,8 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
   p.dyn_in = 0;  // no room for the phase stamps in the fixed scratch
   p.inlist = nullptr;
   p.inrest = nullptr;
+  p.outlist = nullptr;
+  p.outrest = nullptr;
   p.sph = nullptr;
   void* args[] = {&p};
   e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kGridThreads), args, L.smem, st);

@@ -32,7 +32,7 @@ DJ_INF = 2**31 - 1
 
 DJ_MODE_AUTO, DJ_MODE_PHASE, DJ_MODE_PLAIN = 0, 1, 2
 DJ_ENGINE_AUTO, DJ_ENGINE_GRID, DJ_ENGINE_CLUSTER = 0, 1, 2
-DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN, DJ_SETTLE_OUT_DYN_IN = 0, 1, 2, 3
+DJ_SETTLE_AUTO, DJ_SETTLE_OUT, DJ_SETTLE_OUT_IN, DJ_SETTLE_OUT_DYN_IN, DJ_SETTLE_DYN = 0, 1, 2, 3, 4
 DJ_FORMAT_DENSE, DJ_FORMAT_CSR = 0, 1
 DJ_COPIES_AUTO, DJ_COPIES_NARROW, DJ_COPIES_WIDE = 0, 1, 2
 DJ_BATCH_ENGINE_AUTO, DJ_BATCH_ENGINE_CLUSTER, DJ_BATCH_ENGINE_LOCKSTEP = 0, 1, 2

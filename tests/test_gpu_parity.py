@@ -440,6 +440,10 @@ def test_dynamic_in_bound(dj, orc):
             ref = orc.dijkstra(W, s)
             assert_same(solve(dj, G, s, engine=1, settle=3), ref, f"{what} s={s} dynamic IN")
             ph_dyn = dj.dj_last_phases()
+            assert_same(solve(dj, G, s, engine=1, settle=4), ref, f"{what} s={s} dynamic IN and OUT")
+            assert_same(solve(dj, G, s, engine=1, settle=4, rowpush=1), ref, f"{what} s={s} dynamic both, row push")
+            assert_same(solve(dj, G, s, engine=1, settle=4, live=1 << 20, rowpush=-1), ref,
+                        f"{what} s={s} dynamic both, gather")
             assert_same(solve(dj, G, s, engine=1, settle=2), ref, f"{what} s={s} static IN")
             ph_static = dj.dj_last_phases()
             assert_same(solve(dj, G, s, engine=1, settle=1), ref, f"{what} s={s} OUT only")
