@@ -156,15 +156,7 @@ struct Slice {
   int c0;    // first column (node id) of the slice, a multiple of 4
   int sw;    // columns in the slice, a multiple of 4
   int nvec;  // sw / 4
-  // dynamic IN bound (grid engine): the static minimum in-weight of each column (the tie
-  // sources belong to it), and the global word per node recording the phase it settled in
-  const uint32_t* minin0 = nullptr;
-  uint32_t* sph = nullptr;
-  uint32_t sph_stamp = 0;
 };
-
-// Whether column j's IN weight is still the static minimum (its tie sources apply).
-__device__ __forceinline__ bool minin_static(const Slice& s, int j) { return !s.minin0 || s.minin0[j] == s.minin[j]; }
 
 // Global decision of one phase.
 struct Decision {
@@ -554,7 +546,7 @@ __device__ __forceinline__ int live_groups(const Slice& s, const Decision& D, ui
       thr = t > thr ? t : thr;
       if (t == 0) continue;
       const uint32_t d = s.dist[col];
-      if (ties && t < (1ull << 32) && d < kInf && d == D.m + s.minin[col] && minin_static(s, col)) continue;
+      if (ties && t < (1ull << 32) && d < kInf && d == D.m + s.minin[col]) continue;
       if (rows && t == (1ull << 32)) {
         ++nimp;
         continue;
@@ -867,7 +859,7 @@ __device__ __forceinline__ int gather_column_pass(const Slice& s, const int32_t*
       const uint64_t t = column_live(s, col, D, bits_u);
       if (t == 0) continue;
       const uint32_t d = s.dist[col];
-      if (ts.cap > 0 && t < (1ull << 32) && D.use_in && d < kInf && d == D.m + s.minin[col] && minin_static(s, col)) {
+      if (ts.cap > 0 && t < (1ull << 32) && D.use_in && d < kInf && d == D.m + s.minin[col]) {
         tl[atomicAdd(&sc->cnt[28], 1u)] = static_cast<uint32_t>(col);
         continue;
       }
@@ -1286,10 +1278,7 @@ __device__ __forceinline__ void commit_column(const Slice& s, int col, uint64_t 
                                               uint32_t bits_u, Part& pt) {
   const uint32_t d = s.dist[col];
   const uint32_t tie0 = stored_tie(s, col, D, bits_u);
-  if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) {
-    s.vis[col] = 1;
-    if (s.sph) s.sph[s.c0 + col] = s.sph_stamp;
-  }
+  if (!s.vis[col] && in_settled(static_cast<uint32_t>(s.c0 + col), d, in_key(d, s.minin[col]), D)) s.vis[col] = 1;
   commit_key(s, col, b, tie0, D, bits_u);
   column_partial(s, col, pt);
 }
@@ -1403,18 +1392,47 @@ struct DynIn {
   const uint2* olist;  // shared: [sw][kList] (weight, column) of the slice's nodes' out-edges
   const uint32_t* orest;
   uint8_t* ok0;
-  const uint32_t* sph;  // global phase stamps
+  uint32_t* sph;        // global phase stamps (phase + 1 of each node's settlement; the source's 0)
+  uint32_t* pre;        // shared: [sw][2] the stamps the next update checks, fetched ahead
+  uint8_t* stamped;     // shared: [sw] the column's own stamp is written
 };
+// Start fetching (cp.async) the stamps the next dyn_in_update checks, one or two per unsettled
+// column, right after a phase's decision: they arrive while the phase relaxes.  A stamp read this
+// early may miss a settlement of the running phase, which the update's rule ignores anyway.
+template <int kList>
+__device__ __forceinline__ void dyn_in_prefetch(const Slice& s, const DynIn& dy) {
+  for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
+    const bool open = !s.vis[j];
+    const int k = dy.k0[j], ko = dy.olist ? dy.ok0[j] : kList;
+    // each slot is written once: by the copy, or (nothing to check) with all ones
+    if (open && k < kList && dy.list[j * kList + k].x < kInf)
+      cp_async4(dy.pre + 2 * j, dy.sph + dy.list[j * kList + k].y);
+    else
+      dy.pre[2 * j] = 0xFFFFFFFFu;
+    if (open && ko < kList && dy.olist[j * kList + ko].x < kInf)
+      cp_async4(dy.pre + 2 * j + 1, dy.sph + dy.olist[j * kList + ko].y);
+    else
+      dy.pre[2 * j + 1] = 0xFFFFFFFFu;
+  }
+  cp_async_commit();
+}
+// After the commit of phase `phase`: stamp the columns this phase settled (phase + 1), then move
+// the cursors of the unsettled ones.
 template <int kList>
 __device__ __forceinline__ void dyn_in_update(const Slice& s, const DynIn& dy, uint32_t phase) {
+  cp_async_wait_all();  // this thread's prefetches (the same columns it checks below)
   for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
-    if (s.vis[j]) continue;
+    if (s.vis[j]) {
+      if (!dy.stamped[j]) {
+        dy.sph[s.c0 + j] = phase + 1;
+        dy.stamped[j] = 1;
+      }
+      continue;
+    }
     const int k = dy.k0[j], ko = dy.olist ? dy.ok0[j] : kList;
-    const uint2 e = k < kList ? dy.list[j * kList + k] : make_uint2(kInf, 0u);
-    const uint2 eo = ko < kList ? dy.olist[j * kList + ko] : make_uint2(kInf, 0u);
-    // both checks' loads in flight together; an exhausted list (INF entry) keeps its bound
-    const uint32_t sp = e.x < kInf ? __ldcg(dy.sph + e.y) : 0xFFFFFFFFu;
-    const uint32_t spo = eo.x < kInf ? __ldcg(dy.sph + eo.y) : 0xFFFFFFFFu;
+    // an exhausted list (INF entry) keeps its bound: its stamp slot holds all ones
+    const uint32_t sp = k < kList ? dy.pre[2 * j] : 0xFFFFFFFFu;
+    const uint32_t spo = ko < kList ? dy.pre[2 * j + 1] : 0xFFFFFFFFu;
     if (sp <= phase) {
       dy.k0[j] = static_cast<uint8_t>(k + 1);
       s.minin[j] = k + 1 < kList ? dy.list[j * kList + k + 1].x : dy.rest[j];

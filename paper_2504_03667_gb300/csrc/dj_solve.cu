@@ -107,7 +107,9 @@ __device__ __forceinline__ void grid_exit(uint32_t* ctl) {
   }
 }
 
-template <int V, int U>
+// DYN: the dynamic IN (and OUT) bound; a separate instantiation, so that the kernels of other
+// graphs compile without its code.
+template <int V, int U, bool DYN>
 __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, BlockScratch& sc, Decision& s_dec,
                                            uint32_t& s_flag, uint32_t& s_rem) {
   const int G = gridDim.x, b = blockIdx.x;
@@ -146,8 +148,8 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
   q += (static_cast<size_t>(p.swcap) / 4 + 3) / 4 * 16;
   uint32_t* list = reinterpret_cast<uint32_t*>(q);  // staged settled rows
   q += static_cast<size_t>(p.list_cap) * 4;
-  DynIn dy{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, p.sph};
-  if (p.dyn_in) {  // in- (and out-) lists of the slice's nodes, rest bounds, cursors, static minima
+  DynIn dy{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, p.sph, nullptr, nullptr};
+  if (DYN) {  // in- (and out-) lists of the slice's nodes, rest bounds, cursors, prefetched stamps
     const bool dout = (p.dyn_in & 2) != 0;
     uint2* il = reinterpret_cast<uint2*>(q);
     q += static_cast<size_t>(p.swcap) * kInLists * 8;
@@ -157,12 +159,14 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     q += static_cast<size_t>(p.swcap) * 4;
     uint32_t* orr = reinterpret_cast<uint32_t*>(q);
     if (dout) q += static_cast<size_t>(p.swcap) * 4;
-    uint32_t* m0 = reinterpret_cast<uint32_t*>(q);
+    uint8_t* stamped = q;
     q += static_cast<size_t>(p.swcap) * 4;
     uint8_t* k0 = q;
     q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
     uint8_t* ok0 = q;
     if (dout) q += (static_cast<size_t>(p.swcap) + 15) / 16 * 16;
+    dy.pre = reinterpret_cast<uint32_t*>(q);
+    q += static_cast<size_t>(p.swcap) * 8;
     for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
       const int v = s.c0 + j;
       const bool real = v < p.n;
@@ -177,20 +181,19 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
         orr[j] = real ? __ldg(p.outrest + v) : kInf;
         ok0[j] = 0;
       }
-      m0[j] = real ? static_cast<uint32_t>(__ldg(p.minout + p.n + v)) : kInf;
       k0[j] = 0;
+      stamped[j] = (real && v == p.source) ? 1 : 0;
       if (real) p.sph[v] = v == p.source ? 0u : 0xFFFFFFFFu;  // ordered before use by the first barrier
     }
     dy.list = il;
     dy.rest = ir;
     dy.k0 = k0;
+    dy.stamped = stamped;
     if (dout) {
       dy.olist = ol;
       dy.orest = orr;
       dy.ok0 = ok0;
     }
-    s.minin0 = m0;
-    s.sph = p.sph;
   }
   q = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -243,7 +246,6 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
     uint64_t* tr = (p.trace && b == 0 && static_cast<int>(8 * phase + 7) < p.trace_cap - 2) ? p.trace + 8 * phase
                                                                                            : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = global_ns();
-    s.sph_stamp = phase + 1;  // the stamp this phase's commits write (the source's is 0)
     // 1. publish this slice's partial and its candidates (into its own region)
     uint4* out = p.cand + (static_cast<size_t>(phase & 1) * G + b) * p.swcap;
     uint64_t key;
@@ -313,6 +315,7 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
       tr[7] = static_cast<uint64_t>(total);
     }
     if (D.m >= kInf) break;
+    if (DYN) dyn_in_prefetch<kInLists>(s, dy);  // the stamps the post-commit update needs
     // 4. relax this slice with the settled rows: only columns a settled row can
     //    still change take part.  None: nothing to read; a few: load just those
     //    groups; otherwise stream the whole slice through the warps' rings.
@@ -432,7 +435,7 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
       // 5. merge, mark, commit, and the next partial
       commit_partial<V>(s, t, D, merge, p.bits_u, best, part);
     }
-    if (p.dyn_in) {  // the next phase's IN weights: rows settled in earlier phases drop out
+    if (DYN) {  // stamp this phase's settled columns; the next phase's IN weights: rows settled earlier drop out
       __syncthreads();
       dyn_in_update<kInLists>(s, dy, phase);
     }
@@ -446,7 +449,7 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
   }
 }
 
-template <int V, int U, int THREADS>
+template <int V, int U, int THREADS, bool DYN>
 __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BlockScratch sc;
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sssp_grid(const GridParams p) {
   // that kernel's end, but nothing (graph, workspace, outputs) is touched before it has completed
   pdl_launch_dependents();
   pdl_wait();
-  grid_solve<V, U>(p, smem, sc, s_dec, s_flag, s_rem);  // returns early (uniformly per CTA) on a timeout
+  grid_solve<V, U, DYN>(p, smem, sc, s_dec, s_flag, s_rem);  // returns early (uniformly per CTA) on a timeout
   grid_exit(p.ctl);
 }
 
@@ -823,10 +826,10 @@ size_t layout_bytes(const Layout& L, int nwarps, int own_copies, int offs) {
   b += static_cast<size_t>(L.swcap) * 20;                                        // dist, pred, pdist, minout, minin
   b += (static_cast<size_t>(L.swcap) + 15) / 16 * 16;                            // visited
   b += static_cast<size_t>(L.list_cap) * 4;                                      // staged rows
-  if (L.dyn)  // lists, rests and cursors (one or two sets) and the static minima
+  if (L.dyn)  // lists, rests and cursors (one or two sets), stamped flags, prefetched stamps
     b += static_cast<size_t>(L.dyn) * (static_cast<size_t>(L.swcap) * (kInLists * 8 + 4) +
                                        (static_cast<size_t>(L.swcap) + 15) / 16 * 16) +
-         static_cast<size_t>(L.swcap) * 4;
+         static_cast<size_t>(L.swcap) * 12;
   if (L.filter)  // per-column keys, group thresholds, live groups
     b += static_cast<size_t>(L.swcap) * 8 + static_cast<size_t>(L.swcap) / 4 * 8 +
          (static_cast<size_t>(L.swcap) / 4 + 3) / 4 * 16;
@@ -869,19 +872,19 @@ int make_layout(int nvec_cta, int nwarps, int own_copies, int offs, int want_dep
   return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
 }
 
-template <int V>
+template <int V, bool DYN>
 void* grid_kernel() {
-  return reinterpret_cast<void*>(&k_sssp_grid<V, kRowsPerStage, kGridThreads>);
+  return reinterpret_cast<void*>(&k_sssp_grid<V, kRowsPerStage, kGridThreads, DYN>);
 }
 template <int V, class Jobs>
 void* cluster_kernel() {
   return reinterpret_cast<void*>(&k_sssp_cluster<V, kRowsPerStage, kClusterThreads, Jobs>);
 }
-void* grid_kernel_for(int v) {
+void* grid_kernel_for(int v, bool dyn = false) {
   switch (v) {
-    case 1: return grid_kernel<1>();
-    case 2: return grid_kernel<2>();
-    case 4: return grid_kernel<4>();
+    case 1: return dyn ? grid_kernel<1, true>() : grid_kernel<1, false>();
+    case 2: return dyn ? grid_kernel<2, true>() : grid_kernel<2, false>();
+    case 4: return dyn ? grid_kernel<4, true>() : grid_kernel<4, false>();
   }
   return nullptr;
 }
@@ -964,7 +967,7 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
     L.rs_bytes = 0;  // no room for the row buffers: no row split
     if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
   }
-  void* fn = grid_kernel_for(L.V);
+  void* fn = grid_kernel_for(L.V, dyn_in && g->wmin >= 1 && o.settle != DJ_SETTLE_OUT);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
   int occ = 0;
@@ -1044,9 +1047,11 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
   p.gkey = (rs_min > 0 || rp_min > 0)
                ? reinterpret_cast<unsigned long long*>(ws + ctl_bytes + part_bytes + cand_bytes + snap_bytes)
                : nullptr;
-  p.ts = p.use_in && !p.plain && g->tsrc ? TieSources{g->tsrc, g->tcnt, g->tcap} : TieSources{nullptr, nullptr, 0};
   p.sym = g->directed ? 0 : 1;
   p.dyn_in = dyn_in && p.use_in ? (dyn == 2 ? 3 : 1) : 0;  // bit 0: IN lists, bit 1: OUT lists
+  // the tie sources belong to the static minimum in-weight: not used with the dynamic bound
+  p.ts = p.use_in && !p.plain && g->tsrc && !p.dyn_in ? TieSources{g->tsrc, g->tcnt, g->tcap}
+                                                      : TieSources{nullptr, nullptr, 0};
   p.inlist = g->inlist;
   p.inrest = g->inrest;
   p.outlist = g->outlist;
