@@ -315,7 +315,6 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
       tr[7] = static_cast<uint64_t>(total);
     }
     if (D.m >= kInf) break;
-    if (DYN) dyn_in_prefetch<kInLists>(s, dy);  // the stamps the post-commit update needs
     // 4. relax this slice with the settled rows: only columns a settled row can
     //    still change take part.  None: nothing to read; a few: load just those
     //    groups; otherwise stream the whole slice through the warps' rings.
@@ -349,10 +348,14 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
         (nlg <= p.gather_max ||
          (colpass && static_cast<int>(sc.cnt[26]) + max(0, static_cast<int>(sc.cnt[25]) - kMaxRowColumns) <= p.gather_max));
     if (tr && threadIdx.x == 0) tr[7] |= static_cast<uint64_t>(rowsplit ? 0xFFFFu : rowpush ? 0xFFFEu : nlg) << 32;
+    // the stamps the post-commit update needs (a row-push phase fetches them after its compaction,
+    // whose loads of the published lists would otherwise wait behind them)
+    if (DYN && !rowpush) dyn_in_prefetch<kInLists>(s, dy);
     if (rowpush) {
       unsigned long long* gk = p.gkey + static_cast<size_t>(phase & 1) * p.pitch;
       for (int seg = 0; seg < total; seg += p.list_cap) {  // the same segments and lists in every CTA
         const int cnt = compact_settled(get, seg, min(total, seg + p.list_cap), D, p.bits_u, list, &sc);
+        if (DYN && seg == 0) dyn_in_prefetch<kInLists>(s, dy);
         relax_push(list, cnt, G, p.W, p.pitch, D, p.bits_u, gk);
         __syncthreads();  // the list is rewritten by the next segment
       }
