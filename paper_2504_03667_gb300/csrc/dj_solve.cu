@@ -268,34 +268,35 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
       return;
     // 3. global decision and the prefix of candidate counts, from the G partials
     if (warp == 0) {
-      const int per = (G + 31) / 32;  // <= kMaxPartialsPerLane (G <= 320)
-      const int i0 = min(G, lane * per), i1 = min(G, i0 + per);
+      // lane l reads partials l, l + 32, ... (<= kMaxPartialsPerLane each, G <= 320): every load
+      // instruction covers 32 consecutive partials
       uint64_t k = kNoKey;
-      uint32_t l = 0xFFFFFFFFu, sum = 0, rem = 0;
+      uint32_t l = 0xFFFFFFFFu, rem = 0, carry = 0;
       const uint4* part = p.partials + static_cast<size_t>(phase & 1) * G;
       uint4 xs[kMaxPartialsPerLane];
 #pragma unroll
       for (int r = 0; r < kMaxPartialsPerLane; ++r)  // all loads in flight at once
-        xs[r] = (i0 + r < i1) ? __ldcg(part + i0 + r) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
+        xs[r] = 32 * r + lane < G ? __ldcg(part + 32 * r + lane)
+                                  : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u);
 #pragma unroll
       for (int r = 0; r < kMaxPartialsPerLane; ++r) {
+        if (32 * r >= G) break;
         const uint4 x = xs[r];
         const uint64_t kk = (static_cast<uint64_t>(x.y) << 32) | x.x;
         k = kk < k ? kk : k;
         l = min(l, x.z);
-        if (i0 + r < i1) s_off[i0 + r] = sum;
         const uint32_t cnt = packed ? (x.w & 0xFFFFu) : x.w;
-        sum += cnt;
         rem += packed ? (x.w >> 16) : 0u;
-      }
-      uint32_t incl = sum;
+        uint32_t incl = cnt;  // prefix of the counts over this row of 32 partials
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += tt;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += tt;
+        }
+        if (32 * r + lane < G) s_off[32 * r + lane] = carry + incl - cnt;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
       }
-      for (int i = i0; i < i1; ++i) s_off[i] += incl - sum;
-      if (lane == 31) s_off[G] = incl;
+      if (lane == 0) s_off[G] = carry;
       k = warp_min_u64(k);
       l = warp_min_u32(l);
       rem = warp_sum_u32(rem);
