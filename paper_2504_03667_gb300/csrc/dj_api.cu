@@ -60,6 +60,58 @@ int get_ctx(DevCtx** out) {
   return DJ_OK;
 }
 
+static std::mutex g_fn_mu;
+
+static FnSetup* fn_setup(DevCtx* ctx, const void* fn) {  // g_fn_mu held
+  for (auto& f : ctx->fns)
+    if (f.fn == fn) return &f;
+  ctx->fns.push_back(FnSetup{});
+  ctx->fns.back().fn = fn;
+  return &ctx->fns.back();
+}
+
+int raise_smem_limit(const void* fn, int max_smem_optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, fn);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes");
+  const int dyn = max_smem_optin - static_cast<int>(a.sharedSizeBytes);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(dynamic shared memory)");
+  return dyn;
+}
+
+int prepare_function(DevCtx* ctx, const void* fn, size_t smem, bool nonportable) {
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  FnSetup* f = fn_setup(ctx, fn);
+  if (f->smem == 0) {
+    const int dyn = raise_smem_limit(fn, ctx->max_smem_optin);
+    if (dyn < 0) return dyn;  // an error status
+    f->smem = static_cast<size_t>(dyn);
+  }
+  if (smem > f->smem) return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
+  if (nonportable && !f->nonportable) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return cuda_error(e, "non-portable cluster size");
+    f->nonportable = true;
+  }
+  return DJ_OK;
+}
+
+int function_occupancy(DevCtx* ctx, const void* fn, int threads, size_t smem, int* occ) {
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  FnSetup* f = fn_setup(ctx, fn);
+  if (f->occ < 0 || f->occ_smem != smem || f->occ_threads != threads) {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+    f->occ = n;
+    f->occ_smem = smem;
+    f->occ_threads = threads;
+  }
+  *occ = f->occ;
+  return DJ_OK;
+}
+
 static std::mutex g_ws_mu;
 constexpr size_t kMaxStreamWorkspaces = 64;
 

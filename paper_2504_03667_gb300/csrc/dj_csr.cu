@@ -329,11 +329,10 @@ int launch_csr(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, 
   if (smem > static_cast<size_t>(ctx->max_smem_optin) - 1024)
     return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
   void* fn = reinterpret_cast<void*>(&k_sssp_csr);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(csr smem)");
+  if (int rc = prepare_function(ctx, fn, smem, false)) return rc;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kCsrThreads, smem);
-  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (int rc = function_occupancy(ctx, fn, kCsrThreads, smem, &occ)) return rc;
+  cudaError_t e = cudaSuccess;
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "compressed-row solve cannot be resident");
 
   const size_t ctl_bytes = 256;

@@ -75,6 +75,19 @@ struct StreamWs {
   size_t bytes = 0;
 };
 
+// A kernel's launch set-up on one device, done once: its dynamic shared-memory
+// limit raised to all the device allows next to its static shared memory, the
+// non-portable cluster size allowance, and its resident CTAs per SM at the
+// shared memory and block size last queried.
+struct FnSetup {
+  const void* fn = nullptr;
+  size_t smem = 0;  // the limit set (0: not yet)
+  bool nonportable = false;
+  size_t occ_smem = 0;
+  int occ_threads = 0;
+  int occ = -1;
+};
+
 struct DevCtx {
   int device = -1;
   int num_sms = 0;
@@ -83,6 +96,7 @@ struct DevCtx {
   int cluster_launch = 0;
   uint32_t* words = nullptr;  // device: [0] error bits, [1] phases of the last single solve
   std::vector<StreamWs> ws;   // per-stream workspaces of the grid engine (see stream_workspace)
+  std::vector<FnSetup> fns;   // see prepare_function
 };
 
 // error reporting (thread-local message)
@@ -92,6 +106,17 @@ void clear_error();
 
 // per-device context of the current device (created on first use)
 int get_ctx(DevCtx** out);
+
+// Let `fn` launch with `smem` bytes of dynamic shared memory (and, with
+// `nonportable`, clusters of more than 8 CTAs) on ctx's device.  The limit is
+// set once, to the most the device allows, so the driver is asked only on a
+// kernel's first launch (a small solve would otherwise pay those calls every
+// time) and no later call lowers it.
+int prepare_function(DevCtx* ctx, const void* fn, size_t smem, bool nonportable);
+// The same limit for `fn` without a context (the allocation-free entry point).
+int raise_smem_limit(const void* fn, int max_smem_optin);
+// Resident CTAs per SM of `fn` at `threads` x `smem`, queried once per setting.
+int function_occupancy(DevCtx* ctx, const void* fn, int threads, size_t smem, int* occ);
 
 // A device buffer of at least `bytes` kept for stream `st` (its first
 // `zero_bytes` zeroed on `st` when the buffer is created or grown), so that

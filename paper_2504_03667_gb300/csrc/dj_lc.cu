@@ -259,11 +259,10 @@ extern "C" int dj_sssp_lc(const dj_graph* g, int32_t source, int32_t* dist, int3
                       (static_cast<size_t>(G) * swcap / 32 + 1 + 3) / 4 * 16 + (static_cast<size_t>(swcap) + 15) / 16 * 16;
   if (smem > static_cast<size_t>(ctx->max_smem_optin)) return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
   void* fn = lc_kernel_for(V);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(label-correcting smem)");
+  if (int rc = prepare_function(ctx, fn, smem, false)) return rc;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kLcThreads, smem);
-  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (int rc = function_occupancy(ctx, fn, kLcThreads, smem, &occ)) return rc;
+  cudaError_t e = cudaSuccess;
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "label-correcting solve cannot be resident");
 
   const size_t ctl_bytes = 256;

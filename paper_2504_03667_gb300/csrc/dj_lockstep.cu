@@ -536,11 +536,10 @@ int plan_lockstep(const dj_graph* g, int32_t k, LockstepPlan* plan) {
   plan->rstride = static_cast<int>(((static_cast<size_t>(plan->S) + 1 + static_cast<size_t>(plan->S) * swmax + 3) / 4) * 4);
   plan->k = k;
   const void* fn = reinterpret_cast<const void*>(&k_sssp_lockstep);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(plan->smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(lockstep smem)");
+  if (int rc = prepare_function(ctx, fn, plan->smem, false)) return rc;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kLsThreads, plan->smem);
-  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (int rc = function_occupancy(ctx, fn, kLsThreads, plan->smem, &occ)) return rc;
+  cudaError_t e = cudaSuccess;
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "lockstep engine cannot be resident");
   // workspace: control words, partials, decisions, per-block totals and published lists
   const size_t ctl = 256;

@@ -972,11 +972,10 @@ int launch_grid(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred,
     if (int rc = make_layout(nvec_cta, nwarps, 0, G + 1, want_depth, budget, &L)) return rc;
   }
   void* fn = grid_kernel_for(L.V, dyn_in && g->wmin >= 1 && o.settle != DJ_SETTLE_OUT);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
+  if (int rc = prepare_function(ctx, fn, L.smem, false)) return rc;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, L.smem);
-  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  if (int rc = function_occupancy(ctx, fn, kGridThreads, L.smem, &occ)) return rc;
+  cudaError_t e = cudaSuccess;
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "grid engine cannot be resident");
   if (occ < per_sm) return set_error(DJ_EUNSUPPORTED, "requested CTAs per SM cannot be resident");
 
@@ -1099,13 +1098,9 @@ static int cluster_layout(int32_t max_pitch, const ClusterLaunch& cl, Layout* L)
 }
 
 static int prepare_cluster(void* fn, const ClusterLaunch& cl, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(cluster smem)");
-  if (cl.cluster_size > 8) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return cuda_error(e, "non-portable cluster size");
-  }
-  return DJ_OK;
+  DevCtx* ctx = nullptr;
+  if (int rc = get_ctx(&ctx)) return rc;
+  return prepare_function(ctx, fn, smem, cl.cluster_size > 8);
 }
 
 int cluster_max_clusters(int32_t max_pitch, const ClusterLaunch& cl, int* clusters) {
@@ -1366,11 +1361,12 @@ extern "C" int dj_sssp_noalloc(const dj_graph* g, int32_t source, int32_t* dist,
       sizeof(uint4) != kNoAllocEntryBytes)
     return set_error(DJ_EUNSUPPORTED, "internal: scratch layout disagrees with the slice layout");
   void* fn = grid_kernel_for(L.V);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(grid smem)");
+  const int dyn = raise_smem_limit(fn, dv->max_smem_optin);  // as the other entry points: never lowered
+  if (dyn < 0) return dyn;
+  if (L.smem > static_cast<size_t>(dyn)) return set_error(DJ_EUNSUPPORTED, "slice state exceeds shared memory");
   // every CTA must be resident at once (cooperative launch); the query allocates nothing
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, L.smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridThreads, L.smem);
   if (e != cudaSuccess) return cuda_error(e, "occupancy query");
   if (occ < 1) return set_error(DJ_EUNSUPPORTED, "grid engine cannot be resident");
 

@@ -379,6 +379,38 @@ def test_back_to_back_small_solves_keep_stream_order(dj, orc):
     G.free()
 
 
+def test_cuda_graph_capture_and_replay(dj, orc):
+    """Single solves captured into a CUDA graph and replayed (the host's per-call work leaves the
+    loop): on the cluster engine (n=1024, no device memory per solve) and the grid engine (n=4096,
+    a stream-ordered workspace inside the graph), every replay writes the oracle's dist and pred."""
+    import torch
+    for n, pr, seed in ((1024, 0.1, 71), (4096, 0.2, 72)):
+        e = graphgen.bernoulli(n, pr, 1, 100, seed=seed)
+        G = dj.dj_load_edges(e.n, e.src, e.dst, e.w, False)
+        W = orc.build_matrix(e.n, e.src, e.dst, e.w, False)
+        srcs = [int(x) for x in graphgen.sources(n, 6, seed + 1)]
+        Dr, Prr, _ = orc.dijkstra_many_threads(W, np.array(srcs, dtype=np.int32))
+        st = torch.cuda.Stream()
+        D = torch.full((len(srcs), n), -5, dtype=torch.int32, device="cuda")
+        P = torch.full((len(srcs), n), -5, dtype=torch.int32, device="cuda")
+        dj.dj_sssp(G, srcs[0], D[0], P[0], st)  # first launch: the kernel's one-time set-up
+        dj.dj_sync(st)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=st):
+            for i, s in enumerate(srcs):
+                dj.dj_sssp(G, s, D[i], P[i], st)
+        for rep in range(2):
+            with torch.cuda.stream(st):
+                D.fill_(-5)
+                P.fill_(-5)
+                cg.replay()
+            dj.dj_sync(st)
+            for i in range(len(srcs)):
+                assert_same((D[i].cpu().numpy(), P[i].cpu().numpy()), (Dr[i], Prr[i]), f"n={n} replay {rep} #{i}")
+        del cg
+        G.free()
+
+
 def test_back_to_back_grid_solves_and_upload(dj, orc):
     """Grid-engine solves launched back to back (each a programmatic dependent of the previous
     kernel, sharing the stream's workspace), then a matrix upload followed at once by solves on
