@@ -201,8 +201,8 @@ typedef struct dj_solve_opts {
 #define DJ_SETTLE_DYN 4    /* DJ_SETTLE_OUT_DYN_IN and the OUT bound dynamic too: each row's smallest
                               out-weight to columns not yet settled (rows' 4 smallest out-weights listed
                               at load).  A few phases fewer again (85 instead of 89 on that graph), but
-                              the lists take shared memory from the streaming rings (measured slower
-                              there: 1822 against 1739 us), so not the default. */
+                              measured slower there (1700 against 1663 us per solve: its row-push
+                              phases take longer), so not the default. */
 
 /* Fill opts with the defaults (AUTO everything, debug_skip_cta = -1). */
 void dj_solve_opts_init(dj_solve_opts* opts);
@@ -217,7 +217,12 @@ void dj_solve_opts_init(dj_solve_opts* opts);
  * and it is held until the process exits.  While `stream` is being captured
  * into a CUDA graph the solve instead allocates and frees its workspace in
  * stream order (the graph owns it).  The cluster engine (small graphs) needs
- * no workspace: its solve descriptor travels in the launch's parameters.
+ * no workspace: its solve descriptor travels in the launch's parameters.  The
+ * first solve of a kernel configuration on a device sets that kernel's launch
+ * attributes (its shared-memory limit) once; solve once before capturing a
+ * stream under a capture mode that forbids such calls.  Replayed from a CUDA
+ * graph, small solves run without the host's per-call work (n=1024: 3.4 us
+ * per solve against about 11 us from a Python loop).
  * Errors: DJ_EINVAL (source out of range, NULL), DJ_ECUDA (launch failed); a
  * device-side timeout shows at dj_sync(). */
 int dj_sssp(const dj_graph* g, int32_t source, int32_t* dist, int32_t* pred, uint64_t stream);
