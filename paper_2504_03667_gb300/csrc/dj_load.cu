@@ -95,6 +95,104 @@ __global__ void k_rowmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
   }
 }
 
+// Upload from pinned host memory (device-accessible through unified addressing):
+// each warp copies one row at a time from `src` (row stride ld) into the
+// graph's row and takes the row's minimum finite off-diagonal entry on the
+// way, so the matrix crosses the host link once and is not read again for
+// its row minima.  With `vec` (ld a multiple of 4, src 16-byte aligned) the
+// row moves in 16-byte pieces, four in flight per lane, and its last n mod 4
+// entries one by one.  Padding columns are left as they are (INF).  With
+// `ties` (a symmetric matrix, whose column v is row v and whose minin is
+// minout) the warp also lists column u's tie sources as k_tiesrc would: the
+// entries of row u other than the diagonal equal to its minimum, up to cap of
+// them, and their count.
+constexpr int kTieSourceCap = 32;
+__global__ void k_upload_rows(const int32_t* __restrict__ src, int64_t ld, int32_t* __restrict__ W, int64_t pitch,
+                              int32_t n, int32_t* __restrict__ minout, int vec, int ties,
+                              int32_t* __restrict__ tsrc, int32_t* __restrict__ tcnt, int32_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t* s = src + u * ld;
+    int32_t* d = W + u * pitch;
+    uint32_t mn = kInf;
+    auto take = [&](int64_t c, int32_t x) {
+      if (c != u && static_cast<uint32_t>(x) < kInf) mn = min(mn, static_cast<uint32_t>(x));
+    };
+    int64_t done = 0;
+    if (vec) {
+      const int64_t nq = n / 4;
+      const int4* s4 = reinterpret_cast<const int4*>(s);
+      int4* d4 = reinterpret_cast<int4*>(d);
+      for (int64_t q0 = 0; q0 < nq; q0 += 4 * 32) {
+        int4 x[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int64_t q = q0 + 32 * r + lane;
+          x[r] = q < nq ? s4[q] : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int64_t q = q0 + 32 * r + lane;
+          if (q < nq) {
+            d4[q] = x[r];
+            take(4 * q, x[r].x);
+            take(4 * q + 1, x[r].y);
+            take(4 * q + 2, x[r].z);
+            take(4 * q + 3, x[r].w);
+          }
+        }
+      }
+      done = 4 * nq;
+    }
+    for (int64_t c = done + lane; c < n; c += 32) {
+      const int32_t x = s[c];
+      d[c] = x;
+      take(c, x);
+    }
+    mn = warp_min_u32(mn);
+    if (lane == 0) minout[u] = static_cast<int32_t>(mn);
+    if (ties) {
+      __syncwarp();  // the row as every lane wrote it (now in L2)
+      int32_t cnt = 0;
+      const uint32_t lt = (1u << lane) - 1u;
+      auto one = [&](int64_t c, int32_t x) {  // every lane calls it together
+        const bool hit = c < n && c != u && static_cast<uint32_t>(x) == mn;
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int32_t pos = cnt + __popc(bal & lt);
+          if (pos < cap) tsrc[u * cap + pos] = static_cast<int32_t>(c);
+        }
+        cnt += __popc(bal);
+      };
+      if (mn < kInf) {
+        // the row's (device, pitch-aligned) 16-byte pieces, 4 per lane in flight; the list order
+        // is fixed by the loop but immaterial to its users
+        const int64_t nq = (n + 3) / 4;  // pieces covering the row (the last may hold padding: INF)
+        const int4* d4 = reinterpret_cast<const int4*>(d);
+        for (int64_t q0 = 0; q0 < nq; q0 += 4 * 32) {
+          int4 x[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int64_t q = q0 + 32 * r + lane;
+            x[r] = q < nq ? d4[q] : make_int4(int(kInf), int(kInf), int(kInf), int(kInf));
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int64_t c = 4 * (q0 + 32 * r + lane);
+            one(c, x[r].x);
+            one(c + 1, x[r].y);
+            one(c + 2, x[r].z);
+            one(c + 3, x[r].w);
+          }
+        }
+      }
+      if (lane == 0) tcnt[u] = cnt;
+    }
+  }
+}
+
 // minin[v] = min finite W[u][v], u != v.  A block covers 256 columns x kColRows
 // rows (coalesced row reads), keeps a per-column minimum in registers and
 // folds it into minin with one atomicMin per column.  minin starts at INF.
@@ -117,7 +215,6 @@ __global__ void k_colmin(const int32_t* __restrict__ W, int64_t pitch, int32_t n
 // stored dist equals m + minin[v] can only be tied by one of these rows.  A
 // block covers 256 columns x kColRows rows like k_colmin: each thread keeps
 // its column's minin in a register and reads the rows coalesced.
-constexpr int kTieSourceCap = 32;
 __global__ void k_tiesrc(const int32_t* __restrict__ W, int64_t pitch, int32_t n, const int32_t* __restrict__ minin,
                          int32_t* __restrict__ tsrc, int32_t* __restrict__ tcnt, int32_t cap) {
   const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -303,8 +400,11 @@ static void launch_inlists(dj_graph* g, cudaStream_t st) {
 
 // Column minima (a copy of the row minima for undirected graphs, else
 // k_colmin), then the columns' tie sources (and in-lists, where the graph keeps them).
-static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
-  k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
+// Row minima (unless `have_rows`: the upload kernel took them, and on a symmetric matrix the tie
+// sources too), column minima, tie sources and, for graphs that keep them, the in- and out-lists.
+static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st, bool have_rows = false) {
+  if (!have_rows)
+    k_rowmin<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(g->W, g->pitch, g->n, g->minout, stats);
   if (!g->directed) {
     cudaMemcpyAsync(g->minin, g->minout, static_cast<size_t>(g->n) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
   } else {
@@ -312,9 +412,11 @@ static void launch_minima(dj_graph* g, uint32_t* stats, cudaStream_t st) {
     dim3 grid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
     k_colmin<<<grid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin);
   }
-  cudaMemsetAsync(g->tcnt, 0, static_cast<size_t>(g->n) * sizeof(int32_t), st);
-  dim3 tgrid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
-  k_tiesrc<<<tgrid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc, g->tcnt, g->tcap);
+  if (!(have_rows && !g->directed)) {
+    cudaMemsetAsync(g->tcnt, 0, static_cast<size_t>(g->n) * sizeof(int32_t), st);
+    dim3 tgrid(static_cast<unsigned>((g->n + 255) / 256), static_cast<unsigned>((g->n + kColRows - 1) / kColRows));
+    k_tiesrc<<<tgrid, 256, 0, st>>>(g->W, g->pitch, g->n, g->minin, g->tsrc, g->tcnt, g->tcap);
+  }
   if (g->inlist) launch_inlists(g, st);
 }
 
@@ -476,15 +578,27 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
   if (!g || !W || ld < g->n) return set_error(DJ_EINVAL, "need g, W != NULL and ld >= n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (ld == g->n && g->n == g->pitch)  // no padding columns on either side: one contiguous copy
+  // pinned host memory the device can address: one kernel copies the rows and takes their minima
+  cudaPointerAttributes pa;
+  const bool zero_copy = cudaPointerGetAttributes(&pa, W) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                         pa.devicePointer != nullptr;
+  cudaGetLastError();  // an unregistered pointer may leave an error behind on older runtimes
+  if (zero_copy) {
+    const int32_t* src = static_cast<const int32_t*>(pa.devicePointer);
+    const int vec = (ld % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) ? 1 : 0;
+    k_upload_rows<<<grid_for(static_cast<int64_t>(g->n) * 32), 256, 0, st>>>(
+        src, ld, g->W, g->pitch, g->n, g->minout, vec, g->directed ? 0 : 1, g->tsrc, g->tcnt, g->tcap);
+    e = cudaGetLastError();
+  } else if (ld == g->n && g->n == g->pitch) {  // no padding columns on either side: one contiguous copy
     e = cudaMemcpyAsync(g->W, W, static_cast<size_t>(g->n) * g->pitch * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  else
+  } else {
     e = cudaMemcpy2DAsync(g->W, static_cast<size_t>(g->pitch) * sizeof(int32_t), W,
                           static_cast<size_t>(ld) * sizeof(int32_t), static_cast<size_t>(g->n) * sizeof(int32_t),
                           static_cast<size_t>(g->n), cudaMemcpyHostToDevice, st);
+  }
   if (e != cudaSuccess) return cuda_error(e, "host-to-device matrix copy (upload)");
   g->upload_pending = 1;
-  launch_minima(g, nullptr, st);
+  launch_minima(g, nullptr, st, zero_copy);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "row minima");
   return DJ_OK;

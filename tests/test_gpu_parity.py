@@ -347,6 +347,46 @@ def test_host_result_entry_point(dj, orc):
     assert_same((d, p), orc.dijkstra(W2, 42), "after upload")
 
 
+@pytest.mark.parametrize("directed", [True, False], ids=["directed", "undirected"])
+def test_pinned_upload_strides(dj, orc, directed):
+    """dj_graph_upload from pinned host memory copies the rows with a kernel that takes their row
+    minima on the way (and, on an undirected graph, the tie sources from them): with a row stride
+    that is a multiple of 4 (16-byte pieces and an n mod 4 tail), an odd one (entry by entry) and
+    none, on a sparse graph and a dense tie-heavy one, the matrix downloads unchanged and both
+    engines, and the gather in every phase, solve it as the oracle does."""
+    import torch
+    sparse = graphgen.random_edges(1003, 8 * 1003, 1, 9, seed=131 + int(directed), directed=directed)
+    # columns with a few dozen rows of their minimum in-weight: the gather's column pass (phases
+    # of at least 1024 candidates) decides tie-only columns from them
+    dense = (graphgen.random_edges(3001, 40 * 3001, 1, 20, seed=133, directed=True) if directed
+             else graphgen.bernoulli(3001, 0.3, 1, 40, seed=134))
+    rng = np.random.default_rng(7)
+    for kind, e, hi in (("sparse", sparse, 20), ("dense, tie-heavy", dense, 40)):
+        n = e.n
+        G = dj.dj_load_edges(n, e.src, e.dst, e.w, directed)
+        W = orc.build_matrix(n, e.src, e.dst, e.w, directed)
+        for ld in ((n + 8) // 4 * 4, n + 2 if n % 2 else n + 1, n):
+            W2 = W.copy()
+            fin = W2 < P.INF
+            W2[fin] = rng.integers(1, hi, size=int(fin.sum()), dtype=np.int32)  # new weights, same edges
+            np.fill_diagonal(W2, 0)
+            if not directed:
+                W2 = np.minimum(W2, W2.T)
+            buf = torch.full((n, ld), -7, dtype=torch.int32).pin_memory()
+            buf[:, :n] = torch.from_numpy(W2)
+            dj.dj_graph_upload(G, buf[:, :n])
+            dj.dj_sync()
+            assert np.array_equal(dj.dj_graph_download(G), W2), f"{kind} ld={ld}: download"
+            for s in (0, n // 2, n - 1):
+                ref = orc.dijkstra(W2, s)
+                for _, engine in ENGINES:
+                    assert_same(solve(dj, G, s, engine), ref, f"{kind} ld={ld} engine={engine} s={s}")
+                # the gather in every phase: its column pass decides tie-only columns from the tie
+                # sources listed by the upload
+                assert_same(solve(dj, G, s, 1, live=1 << 20), ref, f"{kind} ld={ld} gather s={s}")
+        G.free()
+
+
 def test_back_to_back_small_solves_keep_stream_order(dj, orc):
     """Small-graph solves start while the previous kernel on the stream is still running (they
     are programmatic dependents) and wait for it only before writing their results.  Back to back
