@@ -117,8 +117,12 @@ int dj_load_dense(int32_t n, const int32_t* W, int64_t ld, int w_on_device, uint
  * (host pointer W, row stride ld), then recompute its row and column minima and
  * tie sources.  This is the host-to-device matrix copy of the paper's CUDA
  * accounting (Section III-C, "Memory allocation and data transfer") without a
- * new allocation.  The copy is asynchronous on `stream` when W is pinned;
- * entries are not re-validated (callers pass matrices that came from
+ * new allocation.  The copy is asynchronous on `stream` when W is pinned: a
+ * kernel then reads W over the host link itself and takes the row minima (and,
+ * for an undirected graph, the tie sources) on the way, so the matrix is not
+ * read again for them (W must stay unchanged until the stream reaches it, as
+ * for any asynchronous copy); pageable W goes through an ordinary copy first.
+ * Entries are not re-validated (callers pass matrices that came from
  * dj_graph_download or a validated load, symmetric if the graph was loaded
  * undirected, whose column minima are taken from the row minima).  The next
  * solve of g waits for the kernels before it on its stream before it reads the
