@@ -580,9 +580,9 @@ extern "C" int dj_graph_upload(dj_graph* g, const int32_t* W, int64_t ld, uint64
   cudaError_t e;
   // pinned host memory the device can address: one kernel copies the rows and takes their minima
   cudaPointerAttributes pa;
-  const bool zero_copy = cudaPointerGetAttributes(&pa, W) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-                         pa.devicePointer != nullptr;
-  cudaGetLastError();  // an unregistered pointer may leave an error behind on older runtimes
+  const cudaError_t pe = cudaPointerGetAttributes(&pa, W);
+  if (pe != cudaSuccess) cudaGetLastError();  // clear that query's own status only
+  const bool zero_copy = pe == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
   if (zero_copy) {
     const int32_t* src = static_cast<const int32_t*>(pa.devicePointer);
     const int vec = (ld % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) ? 1 : 0;
