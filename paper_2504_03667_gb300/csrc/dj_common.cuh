@@ -177,24 +177,16 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 
 // ---------------------------------------------------------------- warp / block reductions
+// Warp reductions (every lane of the warp takes part): one redux.sync each for 32-bit values; a
+// 64-bit minimum is the smallest high word, then the smallest low word among the lanes holding it.
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t t = __shfl_xor_sync(0xffffffffu, v, o);
-    v = t < v ? t : v;
-  }
-  return v;
+  const uint32_t hi = __reduce_min_sync(0xffffffffu, static_cast<uint32_t>(v >> 32));
+  const uint32_t lo =
+      __reduce_min_sync(0xffffffffu, static_cast<uint32_t>(v >> 32) == hi ? static_cast<uint32_t>(v) : 0xFFFFFFFFu);
+  return (static_cast<uint64_t>(hi) << 32) | lo;
 }
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) { return __reduce_min_sync(0xffffffffu, v); }
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) { return __reduce_add_sync(0xffffffffu, v); }
 
 __device__ __forceinline__ uint32_t bits_for(uint32_t n) {  // smallest b >= 1 with 2^b >= n
   uint32_t b = 1;
