@@ -184,28 +184,30 @@ __device__ __forceinline__ void slice_init(const Slice& s, int n, int source, co
   }
 }
 
-// Algorithm 1's first step, done at initialisation: every node but the source
-// is at INF, so the first pass settles exactly the source and relaxes its row
-// -- dist[v] = G[s][v] with pred s wherever that is finite (the diagonal never
-// improves the source's own 0).  Call after slice_init; ends synced.
-__device__ __forceinline__ void slice_settle_source(const Slice& s, int n, int source,
-                                                    const int32_t* __restrict__ W, int64_t pitch) {
+// slice_init with Algorithm 1's first step done at once: every node but the
+// source is at INF, so the first pass settles exactly the source and relaxes
+// its row -- dist[v] = G[s][v] with pred s wherever that is finite (the
+// diagonal never improves the source's own 0).  The minima and the source
+// row's entries are loaded together (one round trip instead of two); the
+// caller synchronises the block before the state is used.
+__device__ __forceinline__ void slice_init_source(const Slice& s, int n, int source, const int32_t* minout_g,
+                                                  const int32_t* minin_g, bool need_minout, bool need_minin,
+                                                  const int32_t* __restrict__ W, int64_t pitch) {
   const int32_t* row = W + static_cast<int64_t>(source) * pitch + s.c0;
   for (int j = threadIdx.x; j < s.sw; j += blockDim.x) {
     const int v = s.c0 + j;
-    if (v >= n) continue;
-    if (v == source) {
-      s.vis[j] = 1;
-      continue;
-    }
-    const uint32_t w = static_cast<uint32_t>(__ldg(row + j));
-    if (w < kInf) {
-      s.dist[j] = w;
-      s.pred[j] = source;
-      s.pdist[j] = 0u;
-    }
+    const bool real = v < n;
+    const uint32_t mo = (real && need_minout) ? static_cast<uint32_t>(__ldg(minout_g + v)) : kInf;
+    const uint32_t mi = (real && need_minin) ? static_cast<uint32_t>(__ldg(minin_g + v)) : kInf;
+    const uint32_t w = (real && v != source) ? static_cast<uint32_t>(__ldg(row + j)) : kInf;
+    const bool reached = w < kInf;
+    s.dist[j] = (real && v == source) ? 0u : (reached ? w : kInf);
+    s.pdist[j] = (real && (v == source || reached)) ? 0u : kInf;
+    s.pred[j] = reached ? source : -1;
+    s.vis[j] = (!real || v == source) ? 1 : 0;  // padding columns never take part; the source is settled
+    s.minout[j] = mo;
+    s.minin[j] = mi;
   }
-  __syncthreads();
 }
 
 // Block-wide min of (key64, val32); every thread gets the result.  Ends synced.

@@ -207,11 +207,10 @@ __device__ __forceinline__ void grid_solve(const GridParams& p, uint8_t* smem, B
   q += static_cast<size_t>(nwarps) * p.depth * 4;
   uint32_t* slot_tb = reinterpret_cast<uint32_t*>(q) + static_cast<size_t>(warp) * p.depth * U;
 
-  slice_init(s, p.n, p.source, p.minout, p.minout + p.n, !p.plain, p.use_in && !p.plain);
-  if (!p.plain) {
-    __syncthreads();
-    slice_settle_source(s, p.n, p.source, p.W, p.pitch);
-  }
+  if (p.plain)
+    slice_init(s, p.n, p.source, p.minout, p.minout + p.n, false, false);
+  else
+    slice_init_source(s, p.n, p.source, p.minout, p.minout + p.n, true, p.use_in != 0, p.W, p.pitch);
   const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
   Ring ring;
   ring.buf = rings + static_cast<size_t>(warp) * p.depth * p.srows * p.rowcap;
@@ -672,11 +671,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_sssp_cluster(const ClusterParams
     s.c0 = 4 * v0;
     s.nvec = v1 - v0;
     s.sw = 4 * s.nvec;
-    slice_init(s, d.n, d.source, d.minout, d.minout + d.n, !d.plain, d.use_in && !d.plain);
-    if (!d.plain) {
-      __syncthreads();
-      slice_settle_source(s, d.n, d.source, d.W, d.pitch);
-    }
+    if (d.plain)
+      slice_init(s, d.n, d.source, d.minout, d.minout + d.n, false, false);
+    else
+      slice_init_source(s, d.n, d.source, d.minout, d.minout + d.n, true, d.use_in != 0, d.W, d.pitch);
     const Tile t = make_tile<V>(s.nvec, p.rgs_cap);
     ring.rowbytes = t.active ? static_cast<uint32_t>(max(0, min(32 * V, s.nvec - t.wc * 32 * V)) * 16) : 0u;
     if (threadIdx.x == 0) sc.cnt[32] = 0;
