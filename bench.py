@@ -663,7 +663,7 @@ def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
         c1.synchronize()
         lat.append(c0.elapsed_time(c1) * 1e3)
     # small solves: the same calls captured once into a CUDA graph and replayed, which takes the
-    # host's per-call work (Python, ctypes, the launch) out of the loop
+    # per-launch cost of stream launches (and the host's per-call work) out of the loop
     graph_us = None
     if n < 4096:
         D = torch.empty((16, n), dtype=torch.int32, device="cuda")
@@ -703,7 +703,7 @@ def single_workload(dj, torch, graphgen, name: str, stream, reps: int) -> dict:
     if graph_us is not None:
         out["graph_replay_us_per_solve"] = graph_us
         out["graph_replay_note"] = ("200 dj_sssp calls captured into one CUDA graph, replayed 10 times "
-                                    "(CUDA events): the device-side rate without the host's per-call work")
+                                    "(CUDA events): the rate without the per-launch cost of stream launches")
     return out
 
 
